@@ -1,0 +1,182 @@
+/*
+ * sp.h -- C ABI of the GB300 (sm_103a) spectral-projector library.
+ *
+ * Computes Pi_{<mu}(A) = (I - sign(A - mu I)) / 2 for a symmetric banded A
+ * with the hQDWH algorithm of Kressner & Susnjara, "Fast computation of
+ * spectral projectors of banded matrices" (arXiv 1608.01164): the QDWH
+ * iteration for the matrix sign function (Sec. 2, Eqs. (reccur),
+ * (qdwh_qr_reccur), (qdwh_chol_reccur)) carried out in HODLR format
+ * (Sec. 3.1.1), with one QR-based first step built from Givens rotations
+ * (Sec. 4, Algorithms 1 and 2) and Cholesky-based steps afterwards
+ * (Algorithm 3).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status: SP_OK = 0 or one of the SP_E* codes
+ *    below.  No C++ exception crosses this boundary.  The message of the last
+ *    failure on a context is available from sp_last_error().
+ *  - Dense matrices are column-major with an explicit leading dimension (ld).
+ *    Band input uses LAPACK lower band storage: ab[(i-j) + j*ldab] = A(i,j)
+ *    for 0 <= i-j <= b, ldab >= b+1; entries with i >= n are ignored.
+ *  - Pointers are device or host pointers as stated per argument; where a
+ *    call accepts either, it detects the kind with cudaPointerGetAttributes.
+ *    The caller keeps ownership of every buffer it passes.  sp_ctx_t and
+ *    sp_hodlr_t handles are owned by the library until their *_destroy call.
+ *  - All device work is ordered on the context's CUDA stream.  Calls return
+ *    after enqueueing unless stated otherwise ("synchronising").
+ *  - Arithmetic is IEEE binary64 unless the options select a mixed-precision
+ *    mode.
+ */
+#ifndef SP_H
+#define SP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define SP_OK 0
+#define SP_EINVAL 1      /* invalid argument (size, leaf, tolerance, pointer) */
+#define SP_ENOMEM 2      /* device allocation failed */
+#define SP_ECUDA 3       /* a CUDA runtime call or kernel launch failed */
+#define SP_EBREAKDOWN 4  /* H-Cholesky met a non-positive pivot */
+#define SP_ENONFINITE 5  /* NaN/Inf detected in an iterate */
+#define SP_ERANK 6       /* a truncated rank exceeded the rank capacity */
+#define SP_ETIMEOUT 7    /* a bounded device wait gave up */
+#define SP_EINTERNAL 8   /* internal consistency check failed */
+
+/* Precision modes for sp_qdwh_sign. */
+#define SP_FP64 0        /* every step in binary64 */
+#define SP_MIXED_FP32 1  /* well-conditioned Cholesky steps in residual form with
+                            binary32 leaf/factor GEMMs, binary64 recompression,
+                            then binary64 Newton-Schulz polish */
+
+typedef struct sp_ctx* sp_ctx_t;
+typedef struct sp_hodlr* sp_hodlr_t;
+
+/* Options of the QDWH iteration (Sec. 2.1, Algorithm 3). */
+typedef struct {
+  int max_iter;      /* hard cap on QDWH iterations (default 10) */
+  double delta;      /* stopping tolerance: stop when |1 - l_k| <= delta (default 1e-15) */
+  int precision;     /* SP_FP64 (default) or SP_MIXED_FP32 */
+  int polish_steps;  /* binary64 Newton-Schulz steps X <- X (3I - X^2)/2 after a mixed run (default 1) */
+  double alpha;      /* > 0: use as the bound alpha >= ||A - mu I||_2; 0: estimate it */
+  double l0;         /* > 0: use as the bound l0 <= sigma_min(X_0); 0: estimate it */
+  int qr_steps;      /* number of QR-based steps; the paper uses exactly one (default 1) */
+} sp_qdwh_opts;
+
+/* Diagnostics filled by sp_qdwh_sign (synchronising when non-NULL). */
+typedef struct {
+  int iters;               /* QDWH iterations performed */
+  double alpha, l0;        /* the parameters used */
+  double l[16], a[16], b[16], c[16]; /* l_k, a_k, b_k, c_k per iteration */
+  int kind[16];            /* 1 = QR-based step, 2 = Cholesky-based step, 3 = mixed residual step */
+  int max_rank;            /* largest off-diagonal rank of the result */
+  size_t bytes;            /* device bytes held by the result */
+  double ms_param, ms_qr, ms_chol, ms_total; /* phase times (CUDA events) */
+  double flops;            /* nominal binary64 flops counted by the kernels' task lists */
+} sp_info;
+
+/* Returns opts filled with the defaults listed above. */
+void sp_qdwh_opts_default(sp_qdwh_opts* opts);
+
+/* Creates a context bound to the current CUDA device and the given stream
+ * (a cudaStream_t; NULL selects the legacy default stream).  The context owns
+ * a device workspace that grows on demand. */
+int sp_ctx_create(void* cuda_stream, sp_ctx_t* out);
+void sp_ctx_destroy(sp_ctx_t ctx);
+const char* sp_last_error(sp_ctx_t ctx);
+/* Blocks until all work enqueued on the context's stream has finished and
+ * reports any sticky device error flag (rank overflow, breakdown, timeout). */
+int sp_ctx_sync(sp_ctx_t ctx);
+
+/* HODLR representation of X_0 = A - mu I (Sec. 3.1.1): the index set is split
+ * by balanced bisection into 2^L leaves of at most `leaf` indices (L the
+ * smallest depth with ceil(n / 2^L) <= leaf); leaves are dense and every
+ * off-diagonal block of the band is stored exactly as a rank-b corner
+ * (Lemma 2: a band of width b has off-diagonal rank <= b).
+ *   n >= 1; 1 <= b; leaf >= max(2, 2b) (so band corners stay inside sibling
+ *   blocks); tol > 0 is the absolute truncation tolerance (Sec. 3.1.1,
+ *   "absolute truncation tolerance epsilon") kept with the matrix and used by
+ *   every later formatted operation on it; rank_cap >= 2b is the per-block
+ *   rank capacity (0 selects 160).
+ *   ab: host or device pointer.  On success *out is a new handle. */
+int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
+                       int32_t leaf, double tol, int32_t rank_cap, sp_hodlr_t* out);
+
+/* sign(A - mu I) by hQDWH (Algorithm 3).  A is the handle produced by
+ * sp_hodlr_from_band (it keeps the band, which the QR-based first step
+ * needs).  opts may be NULL (defaults).  On success *sign_out is a new
+ * handle; info (may be NULL) receives diagnostics. */
+int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts, sp_hodlr_t* sign_out, sp_info* info);
+
+/* P = (I - S) / 2 (Algorithm 3, last line); new handle in *P_out. */
+int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out);
+
+/* Y = M X for a HODLR M and a dense n x nrhs block X (HODLR matrix-vector
+ * product, Table "complexity_HODLR": O(k n log n) per column).
+ * X, Y: device pointers, column-major, ldx, ldy >= n; Y must not alias X. */
+int sp_apply(sp_ctx_t ctx, sp_hodlr_t M, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy);
+
+/* Rows row0 .. row0+nrows-1 of M as a dense nrows x n panel (column-major,
+ * ld >= nrows); out: host or device pointer. */
+int sp_to_dense(sp_ctx_t ctx, sp_hodlr_t M, int64_t row0, int64_t nrows, double* out, int64_t ld);
+
+/* tr(M) (sum of the leaves' diagonals).  Synchronising. */
+int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr);
+
+/* Sizes of a handle: order, tree depth, largest off-diagonal rank and device
+ * bytes held.  Synchronising. */
+int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32_t* max_rank, size_t* bytes);
+void sp_hodlr_destroy(sp_hodlr_t M);
+
+/* ---- formatted HODLR arithmetic (Table "complexity_HODLR") ---- */
+
+/* C = alpha A + beta B + gamma I, recompressed at C's tolerance (A's). */
+int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr_t B, double gamma, sp_hodlr_t* C);
+/* C = A * B (formatted product, O(k^2 n log^2 n)). */
+int sp_hodlr_mult(sp_ctx_t ctx, sp_hodlr_t A, sp_hodlr_t B, sp_hodlr_t* C);
+/* Lower-triangular HODLR L with L L^T = Z (H-Cholesky of a symmetric
+ * positive definite Z); SP_EBREAKDOWN on a non-positive leaf pivot. */
+int sp_hodlr_cholesky(sp_ctx_t ctx, sp_hodlr_t Z, sp_hodlr_t* L);
+/* X = op(L)^{-1} B for the lower-triangular HODLR L and a HODLR B (formatted
+ * triangular solve); trans = 0: op(L) = L, trans = 1: op(L) = L^T. */
+int sp_hodlr_trsm(sp_ctx_t ctx, sp_hodlr_t L, int trans, sp_hodlr_t B, sp_hodlr_t* X);
+
+/* ---- parameter estimation (Sec. 5, Eq. (param_estimation)) ---- */
+
+/* counts[i] = #{eigenvalues of A < shifts[i]} (inertia by LDL^T, Sylvester's
+ * law; tridiagonal: Sturm recurrence).  ab, shifts: host or device;
+ * counts: host.  Synchronising. */
+int sp_inertia(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int32_t nshift,
+               const double* shifts, int64_t* counts);
+/* Locates a shift mu with exactly nu eigenvalues below it, mu the midpoint of
+ * the inertia brackets of lambda_nu and lambda_{nu+1}; also returns bounds
+ * lam_nu_hi > lambda_nu and lam_nu1_lo <= lambda_{nu+1}.  Synchronising. */
+int sp_locate_shift(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int64_t nu, double* mu,
+                    double* lam_nu_hi, double* lam_nu1_lo);
+/* QDWH start: alpha >= ||A - mu I||_2 and l0 <= sigma_min((A - mu I)/alpha)
+ * from inertia brackets of the extreme eigenvalues and of the eigenvalues
+ * next to mu.  Synchronising. */
+int sp_qdwh_start(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, double* alpha,
+                  double* l0);
+
+/* ---- QR-based first iteration (Sec. 4, Algorithms 1/2, Remark "construct_off") ---- */
+
+/* Givens rotations of the fast QR of [scale * A; I] for the banded A
+ * (Algorithm 1 for b = 1, Algorithm 2 for b > 1), in the algorithm's order:
+ * rotation t acts on the ordered row pair (p_t, q_t) (0-based rows of the
+ * 2n x n stacked matrix) as [[c, s], [-s, c]] and annihilates the entry of
+ * row q_t.  cs: device pointer to 2 * count doubles (c_0, s_0, c_1, s_1, ...),
+ * count = (2b+1) n - b^2 - b.  ab: device pointer. */
+int sp_givens_generate(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double scale, double* cs);
+/* Q1 and Q2 of [scale * A; I] = [Q1; Q2] R in HODLR format on A's tree
+ * (Remark "construct_off", Theorems 4 and 6: off-diagonal ranks <= 2b). */
+int sp_fastqr_factors(sp_ctx_t ctx, sp_hodlr_t A, double scale, sp_hodlr_t* Q1, sp_hodlr_t* Q2);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP_H */

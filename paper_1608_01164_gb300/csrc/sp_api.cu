@@ -1,0 +1,452 @@
+// sp_api.cu -- the C ABI (include/sp.h) and the hQDWH driver (Algorithm 3).
+//
+// hQDWH for sign(A - mu I) (Sec. 5, Algorithm 3):
+//   alpha, l0 from inertia brackets (reading of Eq. (param_estimation));
+//   X_0 = (A - mu I)/alpha in HODLR (exact: off-diagonal rank b);
+//   k = 0: QR-based step from the Givens rotations of Algorithm 1/2:
+//          X_1 = (b/c) X_0 + (1/sqrt c)(a - b/c) Q1 Q2^T        (Eq. (qdwh_qr))
+//   k >= 1: Cholesky-based steps:
+//          Z = I + c X^2,  L L^T = Z (H-Cholesky),
+//          X <- (b/c) X + (a - b/c) L^{-T} L^{-1} X              (Eq. (qdwh_chol2))
+//          (the paper's (X W^{-1}) W^{-*} with W = L^T, evaluated as two
+//          formatted left solves since X and Z commute and are symmetric)
+//   stop when |1 - l_k| <= delta; P = (I - X)/2.
+// The iteration count depends only on the scalars, so the host runs the
+// scalar recurrence and every matrix operation stays on the device.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "sp_internal.h"
+
+namespace sp {
+void gershgorin(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double* lo, double* hi);
+void locate_shift(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int64_t nu, double* mu,
+                  double* lam_nu_hi, double* lam_nu1_lo);
+void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
+                double* l0);
+void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma);
+int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
+
+namespace {
+
+template <class F>
+int guarded(sp_ctx* ctx, F&& f) {
+  try {
+    f();
+    return SP_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->err = e.msg;
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->err = "host allocation failed";
+    return SP_ENOMEM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->err = e.what();
+    return SP_EINTERNAL;
+  }
+}
+
+bool is_device(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Device copy of a band given as host or device pointer, repacked with
+// ldab = b+1.
+DBuf band_on_device(sp_ctx* ctx, int64_t n, int b, const double* ab, int64_t ldab) {
+  DBuf d((size_t)(b + 1) * n * sizeof(double), ctx->stream);
+  const cudaMemcpyKind kind = is_device(ab) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  check_cuda(cudaMemcpy2DAsync(d.p, sizeof(double) * (b + 1), ab, sizeof(double) * ldab, sizeof(double) * (b + 1), n,
+                               kind, ctx->stream),
+             "band upload");
+  return d;
+}
+
+int read_flags(sp_ctx* ctx) {
+  int h[NFLAGS];
+  check_cuda(cudaMemcpyAsync(h, ctx->d_flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "flags");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  if (h[FLAG_RANK]) return SP_ERANK;
+  if (h[FLAG_BREAKDOWN]) return SP_EBREAKDOWN;
+  if (h[FLAG_NONFINITE]) return SP_ENONFINITE;
+  if (h[FLAG_TIMEOUT]) return SP_ETIMEOUT;
+  return SP_OK;
+}
+
+void check_flags(sp_ctx* ctx, const char* where) {
+  const int f = read_flags(ctx);
+  if (f != SP_OK) {
+    check_cuda(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream), "flags reset");
+    const char* what = f == SP_ERANK ? "rank capacity exceeded" : f == SP_EBREAKDOWN ? "H-Cholesky breakdown"
+                                                              : f == SP_ENONFINITE ? "non-finite value"
+                                                                                   : "device wait timed out";
+    fail(f, std::string(what) + " in " + where);
+  }
+}
+
+struct Owned {
+  sp_hodlr* p = nullptr;
+  explicit Owned(sp_hodlr* q = nullptr) : p(q) {}
+  ~Owned() { hodlr_free(p); }
+  Owned(const Owned&) = delete;
+  Owned& operator=(const Owned&) = delete;
+  void reset(sp_hodlr* q) {
+    hodlr_free(p);
+    p = q;
+  }
+  sp_hodlr* release() {
+    sp_hodlr* q = p;
+    p = nullptr;
+    return q;
+  }
+};
+
+struct Timer {
+  cudaEvent_t a, b;
+  cudaStream_t st;
+  explicit Timer(cudaStream_t s) : st(s) {
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+  }
+  double stop() {
+    cudaEventRecord(b, st);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+  }
+  ~Timer() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
+
+// one Cholesky-based QDWH step: X <- (b/c) X + (a - b/c) Z^{-1} X, Z = I + c X^2
+sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c) {
+  Owned Z(hodlr_mult(ctx, X, X));
+  hodlr_scale_shift(ctx, Z.p, c, 1.0);
+  Owned Lf(hodlr_cholesky(ctx, Z.p));
+  Z.reset(nullptr);
+  Owned Y(hodlr_trsm(ctx, Lf.p, false, X));
+  Owned V(hodlr_trsm(ctx, Lf.p, true, Y.p));
+  Y.reset(nullptr);
+  Lf.reset(nullptr);
+  Owned Xn(hodlr_add(ctx, b / c, X, a - b / c, V.p, 0.0));
+  V.reset(nullptr);
+  hodlr_symmetrize(ctx, Xn.p);
+  return Xn.release();
+}
+
+// QR-based first step on the band kept by A (A = A - mu I in HODLR)
+sp_hodlr* qr_step(sp_ctx* ctx, const sp_hodlr* A, double alpha, double a, double b, double c) {
+  const double sc = std::sqrt(c);
+  sp_hodlr *q1 = nullptr, *q2 = nullptr;
+  fastqr_factors(ctx, A, sc / alpha, &q1, &q2);
+  Owned Q1(q1), Q2(q2);
+  Owned Q2t(hodlr_transpose(ctx, Q2.p));
+  Q2.reset(nullptr);
+  Owned P(hodlr_mult(ctx, Q1.p, Q2t.p));
+  Q1.reset(nullptr);
+  Q2t.reset(nullptr);
+  Owned X1(hodlr_add(ctx, (b / c) / alpha, A, (a - b / c) / sc, P.p, 0.0));
+  hodlr_symmetrize(ctx, X1.p);
+  return X1.release();
+}
+
+}  // namespace
+}  // namespace sp
+
+using namespace sp;
+
+extern "C" {
+
+void sp_qdwh_opts_default(sp_qdwh_opts* o) {
+  if (!o) return;
+  o->max_iter = 10;
+  o->delta = 1e-15;
+  o->precision = SP_FP64;
+  o->polish_steps = 1;
+  o->alpha = 0.0;
+  o->l0 = 0.0;
+  o->qr_steps = 1;
+}
+
+int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
+  if (!out) return SP_EINVAL;
+  auto* ctx = new (std::nothrow) sp_ctx;
+  if (!ctx) return SP_ENOMEM;
+  ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  const int rc = guarded(ctx, [&] {
+    check_cuda(cudaGetDevice(&ctx->device), "cudaGetDevice");
+    check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
+    check_cuda(cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS), "flags");
+    check_cuda(cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS), "flags");
+  });
+  if (rc != SP_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return SP_OK;
+}
+
+void sp_ctx_destroy(sp_ctx_t ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->d_flags) cudaFree(ctx->d_flags);
+  delete ctx;
+}
+
+const char* sp_last_error(sp_ctx_t ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int sp_ctx_sync(sp_ctx_t ctx) {
+  if (!ctx) return SP_EINVAL;
+  return guarded(ctx, [&] { check_flags(ctx, "enqueued work"); });
+}
+
+int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, int32_t leaf,
+                       double tol, int32_t rank_cap, sp_hodlr_t* out) {
+  if (!ctx || !out || !ab) return SP_EINVAL;
+  if (rank_cap == 0) rank_cap = 160;
+  if (n < 1 || b < 1 || ldab < b + 1 || leaf < 2 || leaf < 2 * b || !(tol > 0.0) || rank_cap < 2 * b) {
+    ctx->err = "sp_hodlr_from_band: need n >= 1, b >= 1, ldab >= b+1, leaf >= max(2, 2b), tol > 0, rank_cap >= 2b";
+    return SP_EINVAL;
+  }
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, n, b, ab, ldab);
+    *out = hodlr_from_band(ctx, n, b, d.as<double>(), b + 1, mu, leaf, tol, rank_cap);
+  });
+}
+
+int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hodlr_t* sign_out, sp_info* info) {
+  if (!ctx || !A || !sign_out) return SP_EINVAL;
+  sp_qdwh_opts o;
+  sp_qdwh_opts_default(&o);
+  if (opts_in) o = *opts_in;
+  if (o.max_iter < 1 || o.max_iter > 16 || !(o.delta > 0.0) || o.qr_steps < 0 || o.qr_steps > 1) {
+    ctx->err = "sp_qdwh_sign: invalid options (max_iter in 1..16, delta > 0, qr_steps in {0, 1})";
+    return SP_EINVAL;
+  }
+  if (o.qr_steps == 1 && !A->band) {
+    ctx->err = "sp_qdwh_sign: the QR-based step needs a handle made by sp_hodlr_from_band";
+    return SP_EINVAL;
+  }
+  return guarded(ctx, [&] {
+    sp_info inf;
+    std::memset(&inf, 0, sizeof(inf));
+    ctx->flops = 0.0;
+    Timer total(ctx->stream);
+    double alpha = o.alpha, l0 = o.l0;
+    {
+      Timer t(ctx->stream);
+      if (!(alpha > 0.0) || !(l0 > 0.0)) {
+        if (!A->band) fail(SP_EINVAL, "parameter estimation needs the band (or give alpha and l0)");
+        double ea = 0.0, el = 0.0;
+        qdwh_start(ctx, A->n(), A->b, A->band, A->b + 1, A->mu, &ea, &el);
+        if (!(alpha > 0.0)) alpha = ea;
+        if (!(l0 > 0.0)) l0 = el;
+      }
+      inf.ms_param = t.stop();
+    }
+    inf.alpha = alpha;
+    inf.l0 = l0;
+    // scalar schedule (Eq. (qdwh_parameters_abc)); stop when |1 - l_k| <= delta
+    std::vector<double> as, bs, cs, ls;
+    double l = l0;
+    while (std::fabs(1.0 - l) > o.delta) {
+      if ((int)as.size() >= o.max_iter) fail(SP_EINVAL, "QDWH schedule exceeds max_iter");
+      const double l2 = l * l;
+      const double g = std::cbrt(4.0 * (1.0 - l2) / (l2 * l2));
+      const double sg = std::sqrt(1.0 + g);
+      const double a = sg + 0.5 * std::sqrt(8.0 - 4.0 * g + 8.0 * (2.0 - l2) / (l2 * sg));
+      const double bb = 0.25 * (a - 1.0) * (a - 1.0);
+      const double c = a + bb - 1.0;
+      ls.push_back(l);
+      as.push_back(a);
+      bs.push_back(bb);
+      cs.push_back(c);
+      l = l * (a + bb * l2) / (1.0 + c * l2);
+    }
+    Owned X(nullptr);
+    const int K = (int)as.size();
+    for (int k = 0; k < K; ++k) {
+      inf.l[k] = ls[k];
+      inf.a[k] = as[k];
+      inf.b[k] = bs[k];
+      inf.c[k] = cs[k];
+      Timer t(ctx->stream);
+      if (k == 0 && o.qr_steps == 1) {
+        X.reset(qr_step(ctx, A, alpha, as[k], bs[k], cs[k]));
+        inf.kind[k] = 1;
+        check_flags(ctx, "QR-based step");
+        inf.ms_qr += t.stop();
+      } else {
+        if (!X.p) {
+          X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
+        }
+        X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k]));
+        inf.kind[k] = 2;
+        check_flags(ctx, "Cholesky-based step");
+        inf.ms_chol += t.stop();
+      }
+    }
+    if (!X.p) X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
+    inf.iters = K;
+    inf.ms_total = total.stop();
+    inf.flops = ctx->flops;
+    if (info) {
+      inf.max_rank = hodlr_max_rank(ctx, X.p);
+      inf.bytes = X.p->bytes;
+      *info = inf;
+    }
+    *sign_out = X.release();
+  });
+}
+
+int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out) {
+  if (!ctx || !S || !P_out) return SP_EINVAL;
+  return guarded(ctx, [&] { *P_out = hodlr_add(ctx, -0.5, S, 0.0, nullptr, 0.5); });
+}
+
+int sp_apply(sp_ctx_t ctx, sp_hodlr_t M, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy) {
+  if (!ctx || !M || !X || !Y || nrhs < 0 || ldx < M->n() || ldy < M->n()) return SP_EINVAL;
+  if (nrhs == 0) return SP_OK;
+  return guarded(ctx, [&] {
+    for (int64_t c0 = 0; c0 < nrhs; c0 += 256) {
+      const int w = (int)std::min<int64_t>(256, nrhs - c0);
+      hodlr_apply_level(ctx, M, 0, X + c0 * ldx, ldx, Y + c0 * ldy, ldy, w, nullptr, false, false);
+    }
+  });
+}
+
+int sp_to_dense(sp_ctx_t ctx, sp_hodlr_t M, int64_t row0, int64_t nrows, double* out, int64_t ld) {
+  if (!ctx || !M || !out || row0 < 0 || nrows < 0 || row0 + nrows > M->n() || ld < nrows) return SP_EINVAL;
+  if (nrows == 0) return SP_OK;
+  return guarded(ctx, [&] {
+    if (is_device(out)) {
+      hodlr_to_dense(ctx, M, row0, nrows, out, ld);
+    } else {
+      DBuf d((size_t)nrows * M->n() * sizeof(double), ctx->stream);
+      hodlr_to_dense(ctx, M, row0, nrows, d.as<double>(), nrows);
+      check_cuda(cudaMemcpy2DAsync(out, ld * sizeof(double), d.p, nrows * sizeof(double), nrows * sizeof(double),
+                                   M->n(), cudaMemcpyDeviceToHost, ctx->stream),
+                 "to_dense copy");
+      check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    }
+  });
+}
+
+int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr) {
+  if (!ctx || !M || !tr) return SP_EINVAL;
+  return guarded(ctx, [&] { *tr = hodlr_trace(ctx, M); });
+}
+
+int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32_t* max_rank, size_t* bytes) {
+  if (!ctx || !M) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    if (n) *n = M->n();
+    if (levels) *levels = M->L();
+    if (max_rank) *max_rank = hodlr_max_rank(ctx, M);
+    if (bytes) *bytes = M->bytes;
+  });
+}
+
+void sp_hodlr_destroy(sp_hodlr_t M) { hodlr_free(M); }
+
+int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr_t B, double gamma, sp_hodlr_t* C) {
+  if (!ctx || !A || !C) return SP_EINVAL;
+  if (B && B->tree != A->tree) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    *C = hodlr_add(ctx, alpha, A, beta, B, gamma);
+    check_flags(ctx, "sp_hodlr_add");
+  });
+}
+
+int sp_hodlr_mult(sp_ctx_t ctx, sp_hodlr_t A, sp_hodlr_t B, sp_hodlr_t* C) {
+  if (!ctx || !A || !B || !C || A->tree != B->tree) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    *C = hodlr_mult(ctx, A, B);
+    check_flags(ctx, "sp_hodlr_mult");
+  });
+}
+
+int sp_hodlr_cholesky(sp_ctx_t ctx, sp_hodlr_t Z, sp_hodlr_t* L) {
+  if (!ctx || !Z || !L) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    sp_hodlr* r = hodlr_cholesky(ctx, Z);
+    try {
+      check_flags(ctx, "sp_hodlr_cholesky");
+    } catch (...) {
+      hodlr_free(r);
+      throw;
+    }
+    *L = r;
+  });
+}
+
+int sp_hodlr_trsm(sp_ctx_t ctx, sp_hodlr_t L, int trans, sp_hodlr_t B, sp_hodlr_t* X) {
+  if (!ctx || !L || !B || !X || L->tree != B->tree) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    *X = hodlr_trsm(ctx, L, trans != 0, B);
+    check_flags(ctx, "sp_hodlr_trsm");
+  });
+}
+
+int sp_inertia(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int32_t nshift,
+               const double* shifts, int64_t* counts) {
+  if (!ctx || !ab || !shifts || !counts || n < 1 || b < 0 || ldab < b + 1 || nshift < 0) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, n, b, ab, ldab);
+    DBuf s((size_t)nshift * sizeof(double) + 8, ctx->stream);
+    check_cuda(cudaMemcpyAsync(s.p, shifts, nshift * sizeof(double),
+                               is_device(shifts) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream),
+               "shifts");
+    DBuf c((size_t)nshift * sizeof(int64_t) + 8, ctx->stream);
+    inertia_counts(ctx, n, b, d.as<double>(), b + 1, nshift, s.as<double>(), c.as<int64_t>());
+    check_cuda(cudaMemcpyAsync(counts, c.p, nshift * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream), "counts");
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  });
+}
+
+int sp_locate_shift(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int64_t nu, double* mu,
+                    double* lam_nu_hi, double* lam_nu1_lo) {
+  if (!ctx || !ab || !mu || n < 1 || b < 0 || ldab < b + 1 || nu < 0 || nu > n) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, n, b, ab, ldab);
+    double h1 = 0, h2 = 0;
+    locate_shift(ctx, n, b, d.as<double>(), b + 1, nu, mu, &h1, &h2);
+    if (lam_nu_hi) *lam_nu_hi = h1;
+    if (lam_nu1_lo) *lam_nu1_lo = h2;
+  });
+}
+
+int sp_qdwh_start(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, double* alpha,
+                  double* l0) {
+  if (!ctx || !ab || !alpha || !l0 || n < 1 || b < 0 || ldab < b + 1) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, n, b, ab, ldab);
+    // the counts are of A - mu I's eigenvalues relative to mu: count A at
+    // shifts mu +- d directly
+    qdwh_start(ctx, n, b, d.as<double>(), b + 1, mu, alpha, l0);
+  });
+}
+
+int sp_givens_generate(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double scale, double* cs) {
+  if (!ctx || !ab || !cs || n < 1 || b < 1 || ldab < b + 1) return SP_EINVAL;
+  return guarded(ctx, [&] { givens_generate(ctx, n, b, ab, ldab, 0.0, scale, cs); });
+}
+
+int sp_fastqr_factors(sp_ctx_t ctx, sp_hodlr_t A, double scale, sp_hodlr_t* Q1, sp_hodlr_t* Q2) {
+  if (!ctx || !A || !Q1 || !Q2) return SP_EINVAL;
+  return guarded(ctx, [&] { fastqr_factors(ctx, A, scale, Q1, Q2); });
+}
+
+}  // extern "C"

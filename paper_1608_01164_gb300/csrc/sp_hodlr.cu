@@ -1,0 +1,865 @@
+// sp_hodlr.cu -- HODLR formatted arithmetic (Sec. 3.1.1, Table
+// "complexity_HODLR") built from batched task-list kernels.
+//
+// Notation: for a non-root node c, B_c = M(I_c, I_sib(c)) = U_c V_c^T.
+//
+// Product C = A B (level-parallel form, no recursion).  For c at level l with
+// sibling s and ancestors a' at levels l' < l (s' = sib(a')):
+//   C(I_c, I_s) = A(I_c,I_c) B(I_c,I_s) + A(I_c,I_s) B(I_s,I_s)
+//               + sum_{l'} A(I_c, I_s') B(I_s', I_s)
+//   = [A_sub(c) U^B_c | U^A_c | U^A_a'(I_c) T_a'] [V^B_c | B_sub(s)^T V^A_c | V^B_s'(I_s)]^T
+// with the coupling T_a' = V^A_a'^T U^B_s' (rank^A x rank^B).  So every block of
+// every level is a stack of row-slices of a few n x cap arrays
+//   Y_l = A restricted to level-l diagonal blocks, times U^B_l
+//   Z_l = B^T restricted likewise, times V^A_l
+//   W_l = U^A_l T   (per level-l node)
+// and the whole product is: L restricted applies, two coupling GEMMs, one
+// batched recompression of all blocks, and leaf GEMMs.  Cost O(k^2 n log^2 n).
+//
+// H-Cholesky and the triangular solves are recursive (the factor of the
+// trailing block needs the Schur complement of everything before it); each
+// recursion step enqueues batched kernels (subtree low-rank updates, skinny
+// solves) without host synchronisation.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+// -------------------------------------------------------------------- tree --
+Tree::~Tree() {
+  if (d_lo) cudaFree(d_lo);
+  if (d_sz) cudaFree(d_sz);
+}
+
+std::shared_ptr<Tree> make_tree(int64_t n, int leaf) {
+  auto t = std::make_shared<Tree>();
+  t->n = n;
+  int L = 0;
+  while ((n + (int64_t(1) << L) - 1) >> L > leaf) ++L;
+  t->L = L;
+  const int N = 1 << (L + 1);
+  t->lo.assign(N, 0);
+  t->sz.assign(N, 0);
+  t->lo[1] = 0;
+  t->sz[1] = n;
+  for (int c = 1; c < (1 << L); ++c) {
+    const int64_t m = t->sz[c];
+    t->lo[2 * c] = t->lo[c];
+    t->sz[2 * c] = (m + 1) / 2;
+    t->lo[2 * c + 1] = t->lo[c] + (m + 1) / 2;
+    t->sz[2 * c + 1] = m / 2;
+  }
+  int64_t mx = 0;
+  for (int j = 0; j < (1 << L); ++j) mx = std::max(mx, t->sz[(1 << L) + j]);
+  t->leaf_max = (int)mx;
+  check_cuda(cudaMalloc(&t->d_lo, sizeof(int64_t) * N), "tree alloc");
+  check_cuda(cudaMalloc(&t->d_sz, sizeof(int64_t) * N), "tree alloc");
+  check_cuda(cudaMemcpy(t->d_lo, t->lo.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice), "tree copy");
+  check_cuda(cudaMemcpy(t->d_sz, t->sz.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice), "tree copy");
+  return t;
+}
+
+// ------------------------------------------------------------------ alloc ---
+sp_hodlr* hodlr_alloc(sp_ctx* ctx, std::shared_ptr<Tree> tree, int cap, double tol) {
+  auto* M = new sp_hodlr;
+  M->tree = tree;
+  M->cap = cap;
+  M->tol = tol;
+  M->leaf_ld = tree->leaf_max;
+  const size_t nl = (size_t)tree->nleaves() * M->leaf_ld * M->leaf_ld;
+  const size_t nf = (size_t)std::max(tree->L, 1) * tree->n * cap;
+  try {
+    M->leaves = (double*)dmalloc(nl * sizeof(double), ctx->stream);
+    M->U = (double*)dmalloc(nf * sizeof(double), ctx->stream);
+    M->V = (double*)dmalloc(nf * sizeof(double), ctx->stream);
+    M->rank = (int*)dmalloc(sizeof(int) * tree->nodes(), ctx->stream);
+  } catch (...) {
+    hodlr_free(M);
+    throw;
+  }
+  M->bytes = (nl + 2 * nf) * sizeof(double) + sizeof(int) * tree->nodes();
+  return M;
+}
+
+void hodlr_free(sp_hodlr* M) {
+  if (!M) return;
+  // frees are stream-ordered on the legacy stream: wait for all work first
+  cudaDeviceSynchronize();
+  if (M->leaves) cudaFree(M->leaves);
+  if (M->U) cudaFree(M->U);
+  if (M->V) cudaFree(M->V);
+  if (M->rank) cudaFree(M->rank);
+  if (M->band) cudaFree(M->band);
+  delete M;
+}
+
+void hodlr_set_zero(sp_ctx* ctx, sp_hodlr* M) {
+  const size_t nl = (size_t)M->tree->nleaves() * M->leaf_ld * M->leaf_ld;
+  const size_t nf = (size_t)std::max(M->L(), 1) * M->n() * M->cap;
+  check_cuda(cudaMemsetAsync(M->leaves, 0, nl * sizeof(double), ctx->stream), "memset");
+  check_cuda(cudaMemsetAsync(M->U, 0, nf * sizeof(double), ctx->stream), "memset");
+  check_cuda(cudaMemsetAsync(M->V, 0, nf * sizeof(double), ctx->stream), "memset");
+  check_cuda(cudaMemsetAsync(M->rank, 0, sizeof(int) * M->tree->nodes(), ctx->stream), "memset");
+}
+
+void hodlr_copy(sp_ctx* ctx, const sp_hodlr* S, sp_hodlr* D) {
+  if (S->cap != D->cap || S->tree != D->tree) fail(SP_EINTERNAL, "hodlr_copy shape mismatch");
+  const size_t nl = (size_t)S->tree->nleaves() * S->leaf_ld * S->leaf_ld;
+  const size_t nf = (size_t)std::max(S->L(), 1) * S->n() * S->cap;
+  check_cuda(cudaMemcpyAsync(D->leaves, S->leaves, nl * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
+  check_cuda(cudaMemcpyAsync(D->U, S->U, nf * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
+  check_cuda(cudaMemcpyAsync(D->V, S->V, nf * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
+  check_cuda(cudaMemcpyAsync(D->rank, S->rank, sizeof(int) * S->tree->nodes(), cudaMemcpyDeviceToDevice, ctx->stream),
+             "cp");
+}
+
+std::vector<int> host_ranks(sp_ctx* ctx, const sp_hodlr* M) {
+  std::vector<int> r(M->tree->nodes());
+  check_cuda(cudaMemcpyAsync(r.data(), M->rank, sizeof(int) * r.size(), cudaMemcpyDeviceToHost, ctx->stream), "ranks");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  return r;
+}
+
+namespace {
+
+// ------------------------------------------------------------- from band ----
+// Leaves: dense (A - mu I)(I_j, I_j).  Factors: for a right child c the block
+// B_c = A(I_c, I_{c-1}) is the b x b corner U(ii, t) = A(lo_c + ii, lo_c - b + t)
+// for ii <= t < b with V = [0; I_b] (last b rows of the left sibling); the
+// left child's block is its transpose.  So U_l(I_c) = V_l(I_c) for every node.
+__global__ void k_band_leaves(const double* __restrict__ ab, int64_t ldab, int b, double mu,
+                              const int64_t* __restrict__ lo, const int64_t* __restrict__ sz, int first_leaf,
+                              double* leaves, int ld) {
+  const int j = blockIdx.x;
+  const int node = first_leaf + j;
+  const int64_t l0 = lo[node];
+  const int s = (int)sz[node];
+  double* D = leaves + (size_t)j * ld * ld;
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    double v = 0.0;
+    if (r < s && c < s) {
+      const int d = r - c;
+      const int dd = d < 0 ? -d : d;
+      if (dd <= b) {
+        const int64_t col = l0 + (d >= 0 ? c : r);
+        v = ab[dd + col * ldab];
+        if (d == 0) v -= mu;
+      }
+    }
+    D[r + (size_t)c * ld] = v;
+  }
+}
+
+__global__ void k_band_factors(const double* __restrict__ ab, int64_t ldab, int b, const int64_t* __restrict__ lo,
+                               const int64_t* __restrict__ sz, int64_t n, int cap, double* U, double* V, int* rank) {
+  const int c = blockIdx.x + 2;  // every non-root node
+  const int lev = 31 - __clz(c);
+  const int64_t l0 = lo[c];
+  const int s = (int)sz[c];
+  double* Ul = U + (size_t)(lev - 1) * n * cap + l0;
+  double* Vl = V + (size_t)(lev - 1) * n * cap + l0;
+  const bool right = c & 1;
+  for (int64_t e = threadIdx.x; e < (int64_t)s * cap; e += blockDim.x) {
+    const int ii = (int)(e % s), t = (int)(e / s);
+    double v = 0.0;
+    if (t < b) {
+      if (right) {
+        if (ii <= t) v = ab[(ii + b - t) + (l0 - b + t) * ldab];
+      } else {
+        v = (ii == s - b + t) ? 1.0 : 0.0;
+      }
+    }
+    Ul[ii + (size_t)t * n] = v;
+    Vl[ii + (size_t)t * n] = v;
+  }
+  if (threadIdx.x == 0) rank[c] = b;
+}
+
+// ---------------------------------------------------------------- dense ----
+__device__ __forceinline__ int leaf_of(const int64_t* lo, int first_leaf, int nleaves, int64_t i) {
+  int a = 0, z = nleaves - 1;
+  while (a < z) {
+    const int m = (a + z + 1) / 2;
+    if (lo[first_leaf + m] <= i) a = m;
+    else z = m - 1;
+  }
+  return a;
+}
+
+__global__ void k_to_dense(const double* __restrict__ leaves, int ld, const double* __restrict__ U,
+                           const double* __restrict__ V, const int* __restrict__ rank, const int64_t* __restrict__ lo,
+                           int L, int64_t n, int cap, int64_t row0, int64_t nrows, double* out, int64_t ldo) {
+  const int first_leaf = 1 << L;
+  const int64_t total = nrows * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t ri = e % nrows, j = e / nrows;
+    const int64_t i = row0 + ri;
+    const int li = leaf_of(lo, first_leaf, first_leaf, i), lj = leaf_of(lo, first_leaf, first_leaf, j);
+    double v;
+    if (li == lj) {
+      v = leaves[(size_t)li * ld * ld + (i - lo[first_leaf + li]) + (size_t)(j - lo[first_leaf + li]) * ld];
+    } else {
+      int x = first_leaf + li, y = first_leaf + lj, d = 0;
+      while (x != y) {
+        x >>= 1;
+        y >>= 1;
+        ++d;
+      }
+      const int ci = (first_leaf + li) >> (d - 1);
+      const int lev = L - d + 1;
+      const int r = rank[ci];
+      const double* Ul = U + (size_t)(lev - 1) * n * cap;
+      const double* Vl = V + (size_t)(lev - 1) * n * cap;
+      v = 0.0;
+      for (int t = 0; t < r; ++t) v += Ul[i + (size_t)t * n] * Vl[j + (size_t)t * n];
+    }
+    out[ri + j * ldo] = v;
+  }
+}
+
+__global__ void k_trace(const double* __restrict__ leaves, int ld, const int64_t* __restrict__ sz, int first_leaf,
+                        int nleaves, double* out) {
+  double s = 0.0;
+  for (int j = blockIdx.x; j < nleaves; j += gridDim.x) {
+    const int m = (int)sz[first_leaf + j];
+    const double* D = leaves + (size_t)j * ld * ld;
+    for (int i = threadIdx.x; i < m; i += blockDim.x) s += D[i + (size_t)i * ld];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+}
+
+// ---------------------------------------------------- transpose / sym -------
+__global__ void k_leaf_transpose(const double* __restrict__ S, double* D, int ld, int nleaves) {
+  const int j = blockIdx.x;
+  const double* A = S + (size_t)j * ld * ld;
+  double* B = D + (size_t)j * ld * ld;
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    B[r + (size_t)c * ld] = A[c + (size_t)r * ld];
+  }
+}
+
+__global__ void k_leaf_symmetrize(double* D, int ld) {
+  double* A = D + (size_t)blockIdx.x * ld * ld;
+  for (int e = threadIdx.x; e < ld * ld; e += blockDim.x) {
+    const int r = e % ld, c = e / ld;
+    if (r < c) {
+      const double v = 0.5 * (A[r + (size_t)c * ld] + A[c + (size_t)r * ld]);
+      A[r + (size_t)c * ld] = v;
+      A[c + (size_t)r * ld] = v;
+    }
+  }
+}
+
+__global__ void k_swap_sibling_ranks(const int* __restrict__ src, int* dst, int N) {
+  for (int c = 2 + blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) dst[c] = src[c ^ 1];
+}
+
+__global__ void k_set_int(int* p, int v) {
+  if (threadIdx.x == 0) *p = v;
+}
+
+__global__ void k_max_rank(const int* __restrict__ rank, int N, int* out) {
+  int m = 0;
+  for (int c = 2 + threadIdx.x; c < N; c += blockDim.x) m = max(m, rank[c]);
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, m);
+}
+
+}  // namespace
+
+sp_hodlr* hodlr_from_band(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, int leaf,
+                          double tol, int cap) {
+  auto tree = make_tree(n, leaf);
+  sp_hodlr* M = hodlr_alloc(ctx, tree, cap, tol);
+  try {
+    M->b = b;
+    M->mu = mu;
+    M->band = (double*)dmalloc(sizeof(double) * (size_t)(b + 1) * n, ctx->stream);
+    check_cuda(cudaMemcpy2DAsync(M->band, sizeof(double) * (b + 1), ab_dev, sizeof(double) * ldab,
+                                 sizeof(double) * (b + 1), n, cudaMemcpyDeviceToDevice, ctx->stream),
+               "band copy");
+    check_cuda(cudaMemsetAsync(M->rank, 0, sizeof(int) * tree->nodes(), ctx->stream), "memset");
+    k_band_leaves<<<tree->nleaves(), 256, 0, ctx->stream>>>(M->band, b + 1, b, mu, tree->d_lo, tree->d_sz,
+                                                             tree->nleaves(), M->leaves, M->leaf_ld);
+    check_launch("k_band_leaves");
+    if (tree->L > 0) {
+      k_band_factors<<<tree->nodes() - 2, 256, 0, ctx->stream>>>(M->band, b + 1, b, tree->d_lo, tree->d_sz, n, cap,
+                                                                  M->U, M->V, M->rank);
+      check_launch("k_band_factors");
+    }
+  } catch (...) {
+    hodlr_free(M);
+    throw;
+  }
+  return M;
+}
+
+void hodlr_to_dense(sp_ctx* ctx, const sp_hodlr* M, int64_t row0, int64_t nrows, double* out, int64_t ld) {
+  const int64_t total = nrows * M->n();
+  const int grid = (int)std::min<int64_t>((total + 255) / 256, 8192);
+  k_to_dense<<<std::max(grid, 1), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->U, M->V, M->rank, M->tree->d_lo,
+                                                         M->L(), M->n(), M->cap, row0, nrows, out, ld);
+  check_launch("k_to_dense");
+}
+
+double hodlr_trace(sp_ctx* ctx, const sp_hodlr* M) {
+  DBuf d(sizeof(double), ctx->stream);
+  check_cuda(cudaMemsetAsync(d.p, 0, sizeof(double), ctx->stream), "memset");
+  const int nl = M->tree->nleaves();
+  k_trace<<<std::min(nl, 1024), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->tree->d_sz, nl, nl, d.as<double>());
+  check_launch("k_trace");
+  double h = 0.0;
+  check_cuda(cudaMemcpyAsync(&h, d.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "trace copy");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  return h;
+}
+
+int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M) {
+  DBuf d(sizeof(int), ctx->stream);
+  check_cuda(cudaMemsetAsync(d.p, 0, sizeof(int), ctx->stream), "memset");
+  k_max_rank<<<1, 256, 0, ctx->stream>>>(M->rank, M->tree->nodes(), d.as<int>());
+  check_launch("k_max_rank");
+  int h = 0;
+  check_cuda(cudaMemcpyAsync(&h, d.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "rank copy");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  return h;
+}
+
+// ------------------------------------------------------------------ apply ---
+// Y(I_r) (+)= op(M_sub(r)) X(I_r) for every root r in `roots` (all roots at
+// the same level).  X and Y are indexed by global rows (pointers to row 0).
+static void apply_roots(sp_ctx* ctx, const sp_hodlr* M, const std::vector<int>& roots, const double* X, int64_t ldx,
+                        double* Y, int64_t ldy, int w, const int* pw_node, bool pw_sib, bool trans, bool accumulate) {
+  if (roots.empty() || w <= 0) return;
+  const Tree& T = *M->tree;
+  const int L = T.L;
+  const int rlev = Tree::level_of(roots[0]);
+  auto width_ptr = [&](int node_at_rlev) -> const int* {
+    if (!pw_node) return nullptr;
+    return pw_node + (pw_sib ? (node_at_rlev ^ 1) : node_at_rlev);
+  };
+  // leaves
+  std::vector<GemmTask> leaf;
+  for (int r : roots) {
+    const int d = L - rlev;
+    for (int j = r << d; j < (r + 1) << d; ++j) {
+      const int jl = j - (1 << L);
+      const int64_t l0 = T.lo[j];
+      const int s = (int)T.sz[j];
+      leaf.push_back(gt(M->leaf(jl), M->leaf_ld, X + l0, ldx, Y + l0, ldy, s, w, s, 1.0, accumulate ? 1.0 : 0.0,
+                        nullptr, width_ptr(r), nullptr));
+    }
+  }
+  gemm_batched(ctx, trans, false, leaf);
+  if (rlev >= L) return;
+  // coupling products for all blocks strictly below the roots
+  std::vector<GemmTask> tp;
+  struct Blk {
+    int d;
+    int r;
+  };
+  std::vector<Blk> blks;
+  for (int r : roots)
+    for (int l = rlev + 1; l <= L; ++l) {
+      const int d0 = r << (l - rlev);
+      for (int d = d0; d < d0 + (1 << (l - rlev)); ++d) blks.push_back({d, r});
+    }
+  DBuf tbuf((size_t)blks.size() * M->cap * w * sizeof(double) + 16, ctx->stream);
+  double* tb = tbuf.as<double>();
+  for (size_t i = 0; i < blks.size(); ++i) {
+    const int d = blks[i].d, s = d ^ 1;
+    double* Tm = tb + i * (size_t)M->cap * w;
+    if (!trans) {
+      // T = V_d^T X(I_s)
+      tp.push_back(gt(M->Vc(d), T.n, X + T.lo[s], ldx, Tm, M->cap, M->cap, w, (int)T.sz[s], 1.0, 0.0, M->rank + d,
+                      width_ptr(blks[i].r), nullptr));
+    } else {
+      // (B_d)^T = V_d U_d^T sits at rows I_s: T = U_d^T X(I_d)
+      tp.push_back(gt(M->Uc(d), T.n, X + T.lo[d], ldx, Tm, M->cap, M->cap, w, (int)T.sz[d], 1.0, 0.0, M->rank + d,
+                      width_ptr(blks[i].r), nullptr));
+    }
+  }
+  gemm_batched(ctx, true, false, tp);
+  // accumulate level by level (blocks of one level write disjoint rows)
+  for (int l = rlev + 1; l <= L; ++l) {
+    std::vector<GemmTask> up;
+    for (size_t i = 0; i < blks.size(); ++i) {
+      const int d = blks[i].d;
+      if (Tree::level_of(d) != l) continue;
+      const int s = d ^ 1;
+      const double* Tm = tb + i * (size_t)M->cap * w;
+      if (!trans)
+        up.push_back(gt(M->Uc(d), T.n, Tm, M->cap, Y + T.lo[d], ldy, (int)T.sz[d], w, M->cap, 1.0, 1.0, nullptr,
+                        width_ptr(blks[i].r), M->rank + d));
+      else
+        up.push_back(gt(M->Vc(d), T.n, Tm, M->cap, Y + T.lo[s], ldy, (int)T.sz[s], w, M->cap, 1.0, 1.0, nullptr,
+                        width_ptr(blks[i].r), M->rank + d));
+    }
+    gemm_batched(ctx, false, false, up);
+  }
+}
+
+void hodlr_apply_level(sp_ctx* ctx, const sp_hodlr* M, int lev, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                       int w, const int* pw_node, bool trans, bool accumulate) {
+  std::vector<int> roots;
+  for (int c = 1 << lev; c < (2 << lev); ++c) roots.push_back(c);
+  apply_roots(ctx, M, roots, X, ldx, Y, ldy, w, pw_node, false, trans, accumulate);
+}
+
+static void apply_level_sib(sp_ctx* ctx, const sp_hodlr* M, int lev, const double* X, int64_t ldx, double* Y,
+                            int64_t ldy, int w, const int* pw_node, bool trans) {
+  std::vector<int> roots;
+  for (int c = 1 << lev; c < (2 << lev); ++c) roots.push_back(c);
+  apply_roots(ctx, M, roots, X, ldx, Y, ldy, w, pw_node, true, trans, false);
+}
+
+void hodlr_apply_sub(sp_ctx* ctx, const sp_hodlr* M, int c, const double* X, int64_t ldx, double* Y, int64_t ldy,
+                     int w, const int* pw, bool trans, bool accumulate) {
+  // X, Y point at row lo[c]: shift to global row 0 for apply_roots
+  const int64_t l0 = M->tree->lo[c];
+  // width pointer: a single device int for the whole subtree -> emulate a node
+  // array by passing pw - c (index c gives pw[0])
+  apply_roots(ctx, M, {c}, X - l0, ldx, Y - l0, ldy, w, pw ? pw - c : nullptr, false, trans, accumulate);
+}
+
+// --------------------------------------------------------------------- add --
+sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma) {
+  const int cap = B ? std::max(A->cap, B->cap) : A->cap;
+  sp_hodlr* C = hodlr_alloc(ctx, A->tree, cap, A->tol);
+  try {
+    hodlr_set_zero(ctx, C);
+    const Tree& T = *A->tree;
+    std::vector<LrBlock> blocks;
+    for (int c = 2; c < T.nodes(); ++c) {
+      LrBlock lb;
+      lb.m = (int)T.sz[c];
+      lb.q = (int)T.sz[c ^ 1];
+      if (alpha != 0.0) lb.segs.push_back(Seg{A->Uc(c), A->Vc(c), T.n, T.n, A->cap, A->rank + c, alpha});
+      if (B && beta != 0.0) lb.segs.push_back(Seg{B->Uc(c), B->Vc(c), T.n, T.n, B->cap, B->rank + c, beta});
+      lb.Uout = C->Uc(c);
+      lb.Vout = C->Vc(c);
+      lb.ldu_out = lb.ldv_out = T.n;
+      lb.rank_out = C->rank + c;
+      lb.cap = cap;
+      blocks.push_back(lb);
+    }
+    recompress(ctx, blocks, C->tol);
+    std::vector<AxpbyTask> lt;
+    for (int j = 0; j < T.nleaves(); ++j) {
+      const int s = (int)T.sz[(1 << T.L) + j];
+      lt.push_back(AxpbyTask{A->leaf(j), C->leaf(j), A->leaf_ld, C->leaf_ld, s, s, nullptr, nullptr, alpha, 0.0, gamma});
+    }
+    axpby_batched(ctx, lt);
+    if (B && beta != 0.0) {
+      lt.clear();
+      for (int j = 0; j < T.nleaves(); ++j) {
+        const int s = (int)T.sz[(1 << T.L) + j];
+        lt.push_back(AxpbyTask{B->leaf(j), C->leaf(j), B->leaf_ld, C->leaf_ld, s, s, nullptr, nullptr, beta, 1.0, 0.0});
+      }
+      axpby_batched(ctx, lt);
+    }
+  } catch (...) {
+    hodlr_free(C);
+    throw;
+  }
+  return C;
+}
+
+// In place: M <- alpha M + gamma I (scales the U factors; no recompression).
+void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma) {
+  const Tree& T = *M->tree;
+  std::vector<AxpbyTask> t;
+  for (int l = 1; l <= T.L; ++l)
+    t.push_back(AxpbyTask{nullptr, M->Ul(l), 0, T.n, (int)T.n, M->cap, nullptr, nullptr, 0.0, alpha, 0.0});
+  for (int j = 0; j < T.nleaves(); ++j) {
+    const int s = (int)T.sz[(1 << T.L) + j];
+    t.push_back(AxpbyTask{nullptr, M->leaf(j), 0, M->leaf_ld, s, s, nullptr, nullptr, 0.0, alpha, gamma});
+  }
+  // AxpbyTask with X null and diagonal g: Y = alpha*Y (+gamma on the diagonal
+  // for the leaves only: the factor tasks carry g = 0)
+  axpby_batched(ctx, t);
+}
+
+// -------------------------------------------------------------- transpose ---
+sp_hodlr* hodlr_transpose(sp_ctx* ctx, const sp_hodlr* M) {
+  sp_hodlr* R = hodlr_alloc(ctx, M->tree, M->cap, M->tol);
+  const Tree& T = *M->tree;
+  const size_t nf = (size_t)std::max(T.L, 1) * T.n * M->cap;
+  check_cuda(cudaMemcpyAsync(R->U, M->V, nf * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
+  check_cuda(cudaMemcpyAsync(R->V, M->U, nf * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
+  check_cuda(cudaMemsetAsync(R->rank, 0, sizeof(int) * T.nodes(), ctx->stream), "memset");
+  k_swap_sibling_ranks<<<1, 256, 0, ctx->stream>>>(M->rank, R->rank, T.nodes());
+  check_launch("k_swap_sibling_ranks");
+  k_leaf_transpose<<<T.nleaves(), 256, 0, ctx->stream>>>(M->leaves, R->leaves, M->leaf_ld, T.nleaves());
+  check_launch("k_leaf_transpose");
+  return R;
+}
+
+// M <- (M + M^T)/2: leaves symmetrised, each left-child block recompressed
+// from [U_c | V_s][V_c | U_s]^T / 2 and mirrored into the right sibling.
+void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M) {
+  const Tree& T = *M->tree;
+  k_leaf_symmetrize<<<T.nleaves(), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld);
+  check_launch("k_leaf_symmetrize");
+  if (T.L == 0) return;
+  std::vector<LrBlock> blocks;
+  for (int c = 2; c < T.nodes(); c += 2) {
+    const int s = c + 1;
+    LrBlock lb;
+    lb.m = (int)T.sz[c];
+    lb.q = (int)T.sz[s];
+    lb.segs.push_back(Seg{M->Uc(c), M->Vc(c), T.n, T.n, M->cap, M->rank + c, 0.5});
+    lb.segs.push_back(Seg{M->Vc(s), M->Uc(s), T.n, T.n, M->cap, M->rank + s, 0.5});
+    lb.Uout = M->Uc(c);
+    lb.Vout = M->Vc(c);
+    lb.ldu_out = lb.ldv_out = T.n;
+    lb.rank_out = M->rank + c;
+    lb.cap = M->cap;
+    blocks.push_back(lb);
+  }
+  recompress(ctx, blocks, M->tol);
+  // right sibling s = c+1: U_s = V_c (rows I_s), V_s = U_c (rows I_c)
+  for (int l = 1; l <= T.L; ++l) {
+    for (int c = 1 << l; c < (2 << l); c += 2) {
+      const int s = c + 1;
+      check_cuda(cudaMemcpy2DAsync(M->Uc(s), sizeof(double) * T.n, M->Vc(c), sizeof(double) * T.n,
+                                   sizeof(double) * T.sz[s], M->cap, cudaMemcpyDeviceToDevice, ctx->stream),
+                 "mirror");
+      check_cuda(cudaMemcpy2DAsync(M->Vc(s), sizeof(double) * T.n, M->Uc(c), sizeof(double) * T.n,
+                                   sizeof(double) * T.sz[c], M->cap, cudaMemcpyDeviceToDevice, ctx->stream),
+                 "mirror");
+      check_cuda(cudaMemcpyAsync(M->rank + s, M->rank + c, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream),
+                 "mirror rank");
+    }
+  }
+}
+
+// ---------------------------------------------------------------- product ---
+sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
+  if (A->tree != B->tree) fail(SP_EINVAL, "hodlr_mult: operands on different trees");
+  const Tree& T = *A->tree;
+  const int L = T.L;
+  const int cap = std::max(A->cap, B->cap);
+  sp_hodlr* C = hodlr_alloc(ctx, A->tree, cap, A->tol);
+  try {
+    hodlr_set_zero(ctx, C);
+    if (L == 0) {
+      gemm_batched(ctx, false, false,
+                   {gt(A->leaf(0), A->leaf_ld, B->leaf(0), B->leaf_ld, C->leaf(0), C->leaf_ld, (int)T.n, (int)T.n,
+                       (int)T.n, 1.0, 0.0)});
+      return C;
+    }
+    const size_t lvl = (size_t)T.n * cap;
+    DBuf Yb(lvl * L * sizeof(double), ctx->stream), Zb(lvl * L * sizeof(double), ctx->stream),
+        Wb(lvl * L * sizeof(double), ctx->stream);
+    double* Y = Yb.as<double>();
+    double* Z = Zb.as<double>();
+    double* W = Wb.as<double>();
+    auto Yl = [&](int l) { return Y + (size_t)(l - 1) * lvl; };
+    auto Zl = [&](int l) { return Z + (size_t)(l - 1) * lvl; };
+    auto Wl = [&](int l) { return W + (size_t)(l - 1) * lvl; };
+    // Y_l = A_(level l diag) U^B_l ; Z_l = B^T_(level l diag) V^A_l
+    for (int l = 1; l <= L; ++l) {
+      hodlr_apply_level(ctx, A, l, B->Ul(l), T.n, Yl(l), T.n, B->cap, B->rank, false, false);
+      apply_level_sib(ctx, B, l, A->Vl(l), T.n, Zl(l), T.n, A->cap, A->rank, true);
+    }
+    // couplings T_a = V^A_a^T U^B_sib(a) (rows I_sib(a)); W(I_a) = U^A_a T_a
+    std::vector<GemmTask> tt, wt;
+    DBuf Tb((size_t)T.nodes() * A->cap * B->cap * sizeof(double) + 16, ctx->stream);
+    double* Tm = Tb.as<double>();
+    for (int a = 2; a < T.nodes(); ++a) {
+      const int s = a ^ 1;
+      const int l = Tree::level_of(a);
+      double* Ta = Tm + (size_t)a * A->cap * B->cap;
+      tt.push_back(gt(A->Vc(a), T.n, B->Uc(s), T.n, Ta, A->cap, A->cap, B->cap, (int)T.sz[s], 1.0, 0.0, A->rank + a,
+                      B->rank + s, nullptr));
+      wt.push_back(gt(A->Uc(a), T.n, Ta, A->cap, Wl(l) + T.lo[a], T.n, (int)T.sz[a], B->cap, A->cap, 1.0, 0.0,
+                      nullptr, B->rank + s, A->rank + a));
+    }
+    gemm_batched(ctx, true, false, tt);
+    gemm_batched(ctx, false, false, wt);
+    // off-diagonal blocks of C
+    std::vector<LrBlock> blocks;
+    for (int c = 2; c < T.nodes(); ++c) {
+      const int s = c ^ 1;
+      const int l = Tree::level_of(c);
+      LrBlock lb;
+      lb.m = (int)T.sz[c];
+      lb.q = (int)T.sz[s];
+      lb.segs.push_back(Seg{Yl(l) + T.lo[c], B->Vc(c), T.n, T.n, B->cap, B->rank + c, 1.0});
+      lb.segs.push_back(Seg{A->Uc(c), Zl(l) + T.lo[s], T.n, T.n, A->cap, A->rank + c, 1.0});
+      for (int lp = 1; lp < l; ++lp) {
+        const int ap = c >> (l - lp);
+        lb.segs.push_back(Seg{Wl(lp) + T.lo[c], B->Vl(lp) + T.lo[s], T.n, T.n, B->cap, B->rank + (ap ^ 1), 1.0});
+      }
+      lb.Uout = C->Uc(c);
+      lb.Vout = C->Vc(c);
+      lb.ldu_out = lb.ldv_out = T.n;
+      lb.rank_out = C->rank + c;
+      lb.cap = cap;
+      blocks.push_back(lb);
+    }
+    recompress(ctx, blocks, C->tol);
+    // leaves: A_leaf B_leaf + sum_l W_l(I_c) V^B_l(I_c)^T
+    std::vector<GemmTask> lt;
+    for (int j = 0; j < T.nleaves(); ++j) {
+      const int c = (1 << L) + j;
+      const int s = (int)T.sz[c];
+      lt.push_back(gt(A->leaf(j), A->leaf_ld, B->leaf(j), B->leaf_ld, C->leaf(j), C->leaf_ld, s, s, s, 1.0, 0.0));
+    }
+    gemm_batched(ctx, false, false, lt);
+    for (int lp = 1; lp <= L; ++lp) {
+      lt.clear();
+      for (int j = 0; j < T.nleaves(); ++j) {
+        const int c = (1 << L) + j;
+        const int ap = c >> (L - lp);
+        const int s = (int)T.sz[c];
+        lt.push_back(gt(Wl(lp) + T.lo[c], T.n, B->Vl(lp) + T.lo[c], T.n, C->leaf(j), C->leaf_ld, s, s, B->cap, 1.0,
+                        1.0, nullptr, nullptr, B->rank + (ap ^ 1)));
+      }
+      gemm_batched(ctx, false, true, lt);
+    }
+  } catch (...) {
+    hodlr_free(C);
+    throw;
+  }
+  return C;
+}
+
+// ------------------------------------------------- subtree low-rank update --
+// M_sub(c) += alpha * Ul Ur^T with Ul, Ur: |I_c| x w (pointers at row lo[c],
+// leading dimensions ldl, ldr), width *pw (device) capped by w.
+static void lr_update_sub(sp_ctx* ctx, sp_hodlr* M, int c, const double* Ul, int64_t ldl, const double* Ur,
+                          int64_t ldr, int w, const int* pw, double alpha) {
+  const Tree& T = *M->tree;
+  const int L = T.L;
+  const int lc = Tree::level_of(c);
+  const int64_t l0 = T.lo[c];
+  std::vector<LrBlock> blocks;
+  for (int l = lc + 1; l <= L; ++l) {
+    const int d0 = c << (l - lc);
+    for (int d = d0; d < d0 + (1 << (l - lc)); ++d) {
+      const int s = d ^ 1;
+      LrBlock lb;
+      lb.m = (int)T.sz[d];
+      lb.q = (int)T.sz[s];
+      lb.segs.push_back(Seg{M->Uc(d), M->Vc(d), T.n, T.n, M->cap, M->rank + d, 1.0});
+      lb.segs.push_back(Seg{Ul + (T.lo[d] - l0), Ur + (T.lo[s] - l0), ldl, ldr, w, pw, alpha});
+      lb.Uout = M->Uc(d);
+      lb.Vout = M->Vc(d);
+      lb.ldu_out = lb.ldv_out = T.n;
+      lb.rank_out = M->rank + d;
+      lb.cap = M->cap;
+      blocks.push_back(lb);
+    }
+  }
+  recompress(ctx, blocks, M->tol);
+  std::vector<GemmTask> lt;
+  const int d = L - lc;
+  for (int j = c << d; j < (c + 1) << d; ++j) {
+    const int jl = j - (1 << L);
+    const int s = (int)T.sz[j];
+    lt.push_back(gt(Ul + (T.lo[j] - l0), ldl, Ur + (T.lo[j] - l0), ldr, M->leaf(jl), M->leaf_ld, s, s, w, alpha, 1.0,
+                    nullptr, nullptr, pw));
+  }
+  gemm_batched(ctx, false, true, lt);
+}
+
+// ---------------------------------------------------- skinny solves ---------
+// X(I_c) <- L_c^{-1} X (trans = false) or L_c^{-T} X (trans = true) for the
+// lower-triangular HODLR factor L; X: |I_c| x w (pointer at row lo[c]).
+static void trsm_skinny(sp_ctx* ctx, const sp_hodlr* Lf, int c, double* X, int64_t ldx, int w, const int* pw,
+                        bool trans, double* tmp) {
+  const Tree& T = *Lf->tree;
+  if (Tree::level_of(c) == T.L) {
+    const int jl = c - (1 << T.L);
+    leaf_trsm(ctx, trans, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], X, ldx, w, pw}});
+    return;
+  }
+  const int c1 = 2 * c, c2 = 2 * c + 1;
+  double* X1 = X;
+  double* X2 = X + (T.lo[c2] - T.lo[c]);
+  // L21 = B_{c2} = U_{c2} V_{c2}^T (rows I_c2, cols I_c1)
+  if (!trans) {
+    trsm_skinny(ctx, Lf, c1, X1, ldx, w, pw, false, tmp);
+    // X2 -= U_{c2} (V_{c2}^T X1)
+    gemm_batched(ctx, true, false,
+                 {gt(Lf->Vc(c2), T.n, X1, ldx, tmp, Lf->cap, Lf->cap, w, (int)T.sz[c1], 1.0, 0.0, Lf->rank + c2, pw)});
+    gemm_batched(ctx, false, false,
+                 {gt(Lf->Uc(c2), T.n, tmp, Lf->cap, X2, ldx, (int)T.sz[c2], w, Lf->cap, -1.0, 1.0, nullptr, pw,
+                     Lf->rank + c2)});
+    trsm_skinny(ctx, Lf, c2, X2, ldx, w, pw, false, tmp);
+  } else {
+    trsm_skinny(ctx, Lf, c2, X2, ldx, w, pw, true, tmp);
+    // X1 -= L21^T X2 = V_{c2} (U_{c2}^T X2)
+    gemm_batched(ctx, true, false,
+                 {gt(Lf->Uc(c2), T.n, X2, ldx, tmp, Lf->cap, Lf->cap, w, (int)T.sz[c2], 1.0, 0.0, Lf->rank + c2, pw)});
+    gemm_batched(ctx, false, false,
+                 {gt(Lf->Vc(c2), T.n, tmp, Lf->cap, X1, ldx, (int)T.sz[c1], w, Lf->cap, -1.0, 1.0, nullptr, pw,
+                     Lf->rank + c2)});
+    trsm_skinny(ctx, Lf, c1, X1, ldx, w, pw, true, tmp);
+  }
+}
+
+// ------------------------------------------------------------- H-Cholesky ---
+static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, int c, double* tmp, double* G, double* UG) {
+  const Tree& T = *Lf->tree;
+  if (Tree::level_of(c) == T.L) {
+    const int jl = c - (1 << T.L);
+    leaf_potrf(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], nullptr, 0, 0, nullptr}});
+    return;
+  }
+  const int c1 = 2 * c, c2 = 2 * c + 1;
+  chol_rec(ctx, Lf, c1, tmp, G, UG);
+  // L21 = Z21 L11^{-T}: V_{c2} <- L11^{-1} V_{c2}
+  trsm_skinny(ctx, Lf, c1, Lf->Vc(c2), T.n, Lf->cap, Lf->rank + c2, false, tmp);
+  // Schur complement: Z22 -= U (V^T V) U^T
+  gemm_batched(ctx, true, false,
+               {gt(Lf->Vc(c2), T.n, Lf->Vc(c2), T.n, G, Lf->cap, Lf->cap, Lf->cap, (int)T.sz[c1], 1.0, 0.0,
+                   Lf->rank + c2, Lf->rank + c2)});
+  gemm_batched(ctx, false, false,
+               {gt(Lf->Uc(c2), T.n, G, Lf->cap, UG, T.sz[c2], (int)T.sz[c2], Lf->cap, Lf->cap, 1.0, 0.0, nullptr,
+                   Lf->rank + c2, Lf->rank + c2)});
+  lr_update_sub(ctx, Lf, c2, UG, T.sz[c2], Lf->Uc(c2), T.n, Lf->cap, Lf->rank + c2, -1.0);
+  // the factor is lower triangular: the upper block of node c is zero
+  k_set_int<<<1, 32, 0, ctx->stream>>>(Lf->rank + c1, 0);
+  check_launch("k_set_int");
+  zero_tail_batched(ctx, {ZeroTailTask{Lf->Uc(c1), T.n, (int)T.sz[c1], Lf->rank + c1, Lf->cap},
+                          ZeroTailTask{Lf->Vc(c1), T.n, (int)T.sz[c2], Lf->rank + c1, Lf->cap}});
+  chol_rec(ctx, Lf, c2, tmp, G, UG);
+}
+
+sp_hodlr* hodlr_cholesky(sp_ctx* ctx, const sp_hodlr* Z) {
+  sp_hodlr* Lf = hodlr_alloc(ctx, Z->tree, Z->cap, Z->tol);
+  try {
+    hodlr_copy(ctx, Z, Lf);
+    const Tree& T = *Z->tree;
+    DBuf tmp((size_t)Z->cap * Z->cap * sizeof(double) + 16, ctx->stream);
+    DBuf G((size_t)Z->cap * Z->cap * sizeof(double) + 16, ctx->stream);
+    DBuf UG((size_t)(T.n / 2 + 1) * Z->cap * sizeof(double) + 16, ctx->stream);
+    chol_rec(ctx, Lf, 1, tmp.as<double>(), G.as<double>(), UG.as<double>());
+  } catch (...) {
+    hodlr_free(Lf);
+    throw;
+  }
+  return Lf;
+}
+
+// --------------------------------------------- triangular solve, HODLR RHS --
+struct SolveWs {
+  double* tmp;   // cap x cap
+  double* P;     // n x cap
+  double* K;     // cap x cap
+  double* Ul;    // n x cap
+};
+
+// X_sub(c) <- L_c^{-1} X_sub(c)
+static void solve_rec(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* X, int c, SolveWs& ws) {
+  const Tree& T = *Lf->tree;
+  if (Tree::level_of(c) == T.L) {
+    const int jl = c - (1 << T.L);
+    const int s = (int)T.sz[c];
+    leaf_trsm(ctx, false, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, X->leaf(jl), X->leaf_ld, s, nullptr}});
+    return;
+  }
+  const int c1 = 2 * c, c2 = 2 * c + 1;
+  const int cap = X->cap, capL = Lf->cap;
+  solve_rec(ctx, Lf, X, c1, ws);
+  // X12 = L11^{-1} B12: U_{c1} <- L11^{-1} U_{c1}
+  trsm_skinny(ctx, Lf, c1, X->Uc(c1), T.n, cap, X->rank + c1, false, ws.tmp);
+  // X21 = L22^{-1} (B21 - L21 X11):  L21 X11 = U^L_{c2} (X11^T V^L_{c2})^T
+  hodlr_apply_sub(ctx, X, c1, Lf->Vc(c2), T.n, ws.P, T.sz[c1], capL, Lf->rank + c2, true, false);
+  {
+    LrBlock lb;
+    lb.m = (int)T.sz[c2];
+    lb.q = (int)T.sz[c1];
+    lb.segs.push_back(Seg{X->Uc(c2), X->Vc(c2), T.n, T.n, cap, X->rank + c2, 1.0});
+    lb.segs.push_back(Seg{Lf->Uc(c2), ws.P, T.n, T.sz[c1], capL, Lf->rank + c2, -1.0});
+    lb.Uout = X->Uc(c2);
+    lb.Vout = X->Vc(c2);
+    lb.ldu_out = lb.ldv_out = T.n;
+    lb.rank_out = X->rank + c2;
+    lb.cap = cap;
+    recompress(ctx, {lb}, X->tol);
+  }
+  trsm_skinny(ctx, Lf, c2, X->Uc(c2), T.n, cap, X->rank + c2, false, ws.tmp);
+  // X22 <- B22 - L21 X12 = B22 - U^L_{c2} (V^L_{c2}^T U^X_{c1}) V^X_{c1}^T
+  gemm_batched(ctx, true, false,
+               {gt(Lf->Vc(c2), T.n, X->Uc(c1), T.n, ws.K, capL, capL, cap, (int)T.sz[c1], 1.0, 0.0, Lf->rank + c2,
+                   X->rank + c1)});
+  gemm_batched(ctx, false, false,
+               {gt(Lf->Uc(c2), T.n, ws.K, capL, ws.Ul, T.sz[c2], (int)T.sz[c2], cap, capL, 1.0, 0.0, nullptr,
+                   X->rank + c1, Lf->rank + c2)});
+  lr_update_sub(ctx, X, c2, ws.Ul, T.sz[c2], X->Vc(c1), T.n, cap, X->rank + c1, -1.0);
+  solve_rec(ctx, Lf, X, c2, ws);
+}
+
+// X_sub(c) <- L_c^{-T} X_sub(c)
+static void solveT_rec(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* X, int c, SolveWs& ws) {
+  const Tree& T = *Lf->tree;
+  if (Tree::level_of(c) == T.L) {
+    const int jl = c - (1 << T.L);
+    const int s = (int)T.sz[c];
+    leaf_trsm(ctx, true, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, X->leaf(jl), X->leaf_ld, s, nullptr}});
+    return;
+  }
+  const int c1 = 2 * c, c2 = 2 * c + 1;
+  const int cap = X->cap, capL = Lf->cap;
+  solveT_rec(ctx, Lf, X, c2, ws);
+  // X21 = L22^{-T} B21: U_{c2} <- L22^{-T} U_{c2}
+  trsm_skinny(ctx, Lf, c2, X->Uc(c2), T.n, cap, X->rank + c2, true, ws.tmp);
+  // X12 = L11^{-T} (B12 - L21^T X22), L21^T X22 = V^L_{c2} (X22^T U^L_{c2})^T
+  hodlr_apply_sub(ctx, X, c2, Lf->Uc(c2), T.n, ws.P, T.sz[c2], capL, Lf->rank + c2, true, false);
+  {
+    LrBlock lb;
+    lb.m = (int)T.sz[c1];
+    lb.q = (int)T.sz[c2];
+    lb.segs.push_back(Seg{X->Uc(c1), X->Vc(c1), T.n, T.n, cap, X->rank + c1, 1.0});
+    lb.segs.push_back(Seg{Lf->Vc(c2), ws.P, T.n, T.sz[c2], capL, Lf->rank + c2, -1.0});
+    lb.Uout = X->Uc(c1);
+    lb.Vout = X->Vc(c1);
+    lb.ldu_out = lb.ldv_out = T.n;
+    lb.rank_out = X->rank + c1;
+    lb.cap = cap;
+    recompress(ctx, {lb}, X->tol);
+  }
+  trsm_skinny(ctx, Lf, c1, X->Uc(c1), T.n, cap, X->rank + c1, true, ws.tmp);
+  // X11 <- B11 - L21^T X21 = B11 - V^L_{c2} (U^L_{c2}^T U^X_{c2}) V^X_{c2}^T
+  gemm_batched(ctx, true, false,
+               {gt(Lf->Uc(c2), T.n, X->Uc(c2), T.n, ws.K, capL, capL, cap, (int)T.sz[c2], 1.0, 0.0, Lf->rank + c2,
+                   X->rank + c2)});
+  gemm_batched(ctx, false, false,
+               {gt(Lf->Vc(c2), T.n, ws.K, capL, ws.Ul, T.sz[c1], (int)T.sz[c1], cap, capL, 1.0, 0.0, nullptr,
+                   X->rank + c2, Lf->rank + c2)});
+  lr_update_sub(ctx, X, c1, ws.Ul, T.sz[c1], X->Vc(c2), T.n, cap, X->rank + c2, -1.0);
+  solveT_rec(ctx, Lf, X, c1, ws);
+}
+
+sp_hodlr* hodlr_trsm(sp_ctx* ctx, const sp_hodlr* Lf, bool trans, const sp_hodlr* B) {
+  if (Lf->tree != B->tree) fail(SP_EINVAL, "hodlr_trsm: operands on different trees");
+  sp_hodlr* X = hodlr_alloc(ctx, B->tree, B->cap, B->tol);
+  try {
+    hodlr_copy(ctx, B, X);
+    const Tree& T = *B->tree;
+    const int cm = std::max(B->cap, Lf->cap);
+    DBuf tmp((size_t)cm * cm * sizeof(double) + 16, ctx->stream);
+    DBuf P((size_t)(T.n / 2 + 1) * cm * sizeof(double) + 16, ctx->stream);
+    DBuf K((size_t)cm * cm * sizeof(double) + 16, ctx->stream);
+    DBuf Ul((size_t)(T.n / 2 + 1) * cm * sizeof(double) + 16, ctx->stream);
+    SolveWs ws{tmp.as<double>(), P.as<double>(), K.as<double>(), Ul.as<double>()};
+    if (!trans) solve_rec(ctx, Lf, X, 1, ws);
+    else solveT_rec(ctx, Lf, X, 1, ws);
+  } catch (...) {
+    hodlr_free(X);
+    throw;
+  }
+  return X;
+}
+
+}  // namespace sp

@@ -1,0 +1,263 @@
+// sp_param.cu -- inertia counts and the QDWH start parameters.
+//
+// The paper starts QDWH with alpha ~ ||A||_2 and l0 ~ sigma_min(A/alpha)
+// (Sec. 5, Eq. (param_estimation)).  QDWH needs alpha >= ||A - mu I||_2 and
+// l0 <= sigma_min((A - mu I)/alpha); both follow from eigenvalue brackets, and
+// brackets follow from inertia counts nu(sigma) = #{lambda < sigma}
+// (Sylvester's law of inertia on A - sigma I = L D L^T).  Each thread counts
+// one shift: the tridiagonal Sturm recurrence d_i = (a_i - sigma) -
+// e_{i-1}^2 / d_{i-1}, or for b > 1 the unpivoted banded LDL^T with the last b
+// columns of L kept in a per-thread ring.  A count is a sequential chain of n
+// dependent divisions (latency-bound), so many shifts run side by side.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include <vector>
+
+#include "sp_internal.h"
+
+namespace sp {
+namespace {
+
+__global__ void k_inertia(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+                          const double* __restrict__ shifts, int nshift, int64_t* __restrict__ counts, double pivmin,
+                          double* __restrict__ ring) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nshift) return;
+  const double sigma = shifts[t];
+  int64_t cnt = 0;
+  if (b == 1) {
+    double d = 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double e = (i == 0) ? 0.0 : ab[1 + (i - 1) * ldab];
+      d = (ab[i * ldab] - sigma) - ((i == 0) ? 0.0 : e * e / d);
+      if (fabs(d) < pivmin) d = -pivmin;
+      cnt += d < 0.0;
+    }
+  } else if (b == 0) {
+    for (int64_t i = 0; i < n; ++i) cnt += ab[i * ldab] < sigma;
+  } else {
+    // ring: column k of L (entries L(k+1..k+b, k)) at slot k % b, plus D_k
+    double* Lr = ring + (size_t)t * (b * b + b);
+    double* Dr = Lr + b * b;
+    for (int64_t j = 0; j < n; ++j) {
+      double dj = ab[j * ldab] - sigma;
+      const int64_t k0 = j - b > 0 ? j - b : 0;
+      for (int64_t k = k0; k < j; ++k) {
+        const double l = Lr[(k % b) * b + (j - k - 1)];
+        dj -= l * l * Dr[k % b];
+      }
+      if (fabs(dj) < pivmin) dj = -pivmin;
+      cnt += dj < 0.0;
+      const double inv = 1.0 / dj;
+      double* Lj = Lr + (j % b) * b;
+      for (int64_t i = j + 1; i <= j + b; ++i) {
+        double s = (i < n) ? ab[(i - j) + j * ldab] : 0.0;
+        const int64_t kk0 = i - b > 0 ? i - b : 0;
+        for (int64_t k = kk0; k < j; ++k) s -= Lr[(k % b) * b + (i - k - 1)] * Lr[(k % b) * b + (j - k - 1)] * Dr[k % b];
+        Lj[i - j - 1] = s * inv;
+      }
+      Dr[j % b] = dj;
+    }
+  }
+  counts[t] = cnt;
+}
+
+__global__ void k_gershgorin(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, double* out) {
+  double lo = 1e300, hi = -1e300;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double r = 0.0;
+    for (int d = 1; d <= b; ++d) {
+      if (i + d < n) r += fabs(ab[d + i * ldab]);
+      if (i - d >= 0) r += fabs(ab[d + (i - d) * ldab]);
+    }
+    lo = fmin(lo, ab[i * ldab] - r);
+    hi = fmax(hi, ab[i * ldab] + r);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    const int w = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    out[2 * w] = lo;
+    out[2 * w + 1] = hi;
+  }
+}
+
+__global__ void k_absmax(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, double* out) {
+  double m = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d <= b; ++d)
+      if (i + d < n) m = fmax(m, fabs(ab[d + i * ldab]));
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) out[blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32] = m;
+}
+
+}  // namespace
+
+// counts_dev[i] = #{lambda < shifts_dev[i]} (device arrays)
+void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
+                    const double* shifts_dev, int64_t* counts_dev) {
+  if (nshift <= 0) return;
+  // pivmin = DBL_MIN * max(1, max|a_ij|^2)
+  const int gb = 64, tb = 256;
+  DBuf part((size_t)gb * (tb / 32) * sizeof(double), ctx->stream);
+  k_absmax<<<gb, tb, 0, ctx->stream>>>(ab_dev, ldab, n, b, part.as<double>());
+  check_launch("k_absmax");
+  std::vector<double> h(gb * (tb / 32));
+  check_cuda(cudaMemcpyAsync(h.data(), part.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "cp");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  double amax = 1.0;
+  for (double v : h) amax = std::max(amax, v);
+  const double pivmin = DBL_MIN * amax * amax;
+  DBuf ring(b > 1 ? (size_t)nshift * (b * b + b) * sizeof(double) : 16, ctx->stream);
+  k_inertia<<<(nshift + 63) / 64, 64, 0, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev, pivmin,
+                                                        ring.as<double>());
+  check_launch("k_inertia");
+}
+
+// Gershgorin interval of the band (device input), synchronising.
+void gershgorin(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double* lo, double* hi) {
+  const int gb = 64, tb = 256;
+  DBuf part((size_t)gb * (tb / 32) * 2 * sizeof(double), ctx->stream);
+  k_gershgorin<<<gb, tb, 0, ctx->stream>>>(ab_dev, ldab, n, b, part.as<double>());
+  check_launch("k_gershgorin");
+  std::vector<double> h(gb * (tb / 32) * 2);
+  check_cuda(cudaMemcpyAsync(h.data(), part.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "cp");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  double l = 1e300, u = -1e300;
+  for (size_t i = 0; i < h.size(); i += 2) {
+    l = std::min(l, h[i]);
+    u = std::max(u, h[i + 1]);
+  }
+  *lo = l;
+  *hi = u;
+}
+
+// Host-side multisection driver: evaluates counts at a batch of shifts.
+static std::vector<int64_t> counts_at(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab,
+                                      const std::vector<double>& x) {
+  DBuf sx = upload(x, ctx->stream);
+  DBuf cn(x.size() * sizeof(int64_t) + 8, ctx->stream);
+  inertia_counts(ctx, n, b, ab_dev, ldab, (int)x.size(), sx.as<double>(), cn.as<int64_t>());
+  std::vector<int64_t> h(x.size());
+  check_cuda(cudaMemcpyAsync(h.data(), cn.p, h.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream), "cp");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  return h;
+}
+
+// Brackets [x_k, y_k) of lambda_k for each requested k (1-based) by
+// multisection: count(x) < k <= count(y).  rel: stop when y - x <= rel*scale.
+static void bracket(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, const std::vector<int64_t>& ks,
+                    double glo, double ghi, double rel, std::vector<double>& xs, std::vector<double>& ys) {
+  const int P = 255;  // interior points per bracket and round
+  const size_t K = ks.size();
+  xs.assign(K, glo);
+  ys.assign(K, ghi);
+  const double scale = std::max({1.0, std::fabs(glo), std::fabs(ghi)});
+  for (int round = 0; round < 12; ++round) {
+    std::vector<double> pts;
+    std::vector<size_t> owner;
+    for (size_t k = 0; k < K; ++k) {
+      if (ys[k] - xs[k] <= rel * scale) continue;
+      for (int p = 1; p <= P; ++p) {
+        pts.push_back(xs[k] + (ys[k] - xs[k]) * p / (P + 1));
+        owner.push_back(k);
+      }
+    }
+    if (pts.empty()) break;
+    std::vector<int64_t> c = counts_at(ctx, n, b, ab_dev, ldab, pts);
+    for (size_t t = 0; t < pts.size(); ++t) {
+      const size_t k = owner[t];
+      if (c[t] >= ks[k]) ys[k] = std::min(ys[k], pts[t]);
+      else xs[k] = std::max(xs[k], pts[t]);
+    }
+  }
+}
+
+void locate_shift(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int64_t nu, double* mu,
+                  double* lam_nu_hi, double* lam_nu1_lo) {
+  double glo, ghi;
+  gershgorin(ctx, n, b, ab_dev, ldab, &glo, &ghi);
+  const double pad = 1e-12 * std::max({1.0, std::fabs(glo), std::fabs(ghi)});
+  glo -= pad;
+  ghi += pad;
+  if (nu <= 0) {
+    std::vector<double> x, y;
+    bracket(ctx, n, b, ab_dev, ldab, {1}, glo, ghi, 1e-3, x, y);
+    *mu = x[0] - 1.0;
+    *lam_nu_hi = *mu;
+    *lam_nu1_lo = x[0];
+    return;
+  }
+  if (nu >= n) {
+    std::vector<double> x, y;
+    bracket(ctx, n, b, ab_dev, ldab, {n}, glo, ghi, 1e-3, x, y);
+    *mu = y[0] + 1.0;
+    *lam_nu_hi = y[0];
+    *lam_nu1_lo = *mu;
+    return;
+  }
+  std::vector<double> x, y;
+  bracket(ctx, n, b, ab_dev, ldab, {nu, nu + 1}, glo, ghi, 1e-15, x, y);
+  *lam_nu_hi = y[0];
+  *lam_nu1_lo = x[1];
+  *mu = 0.5 * (y[0] + x[1]);
+  std::vector<int64_t> c = counts_at(ctx, n, b, ab_dev, ldab, {*mu});
+  if (c[0] != nu) fail(SP_EINVAL, "no shift separates lambda_nu and lambda_nu+1 at working precision");
+}
+
+// alpha >= ||A - mu I||_2 from brackets of the extreme eigenvalues, l0 from
+// the largest d on a geometric then linear grid with count(mu-d) == count(mu)
+// == count(mu+d) (no eigenvalue within distance d of mu).
+void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
+                double* l0) {
+  double glo, ghi;
+  gershgorin(ctx, n, b, ab_dev, ldab, &glo, &ghi);
+  const double pad = 1e-12 * std::max({1.0, std::fabs(glo), std::fabs(ghi)});
+  glo -= pad;
+  ghi += pad;
+  std::vector<double> x, y;
+  bracket(ctx, n, b, ab_dev, ldab, {1, n}, glo, ghi, 2e-3, x, y);
+  const double lam_min_lo = x[0], lam_max_hi = y[1];
+  const double a = std::max(mu - lam_min_lo, lam_max_hi - mu) * (1.0 + 1e-10);
+  // distance to the spectrum
+  std::vector<double> pts;
+  std::vector<double> ds;
+  pts.push_back(mu);
+  for (int k = 0; k <= 60; ++k) {
+    const double d = a * std::ldexp(1.0, -k);
+    ds.push_back(d);
+    pts.push_back(mu - d);
+    pts.push_back(mu + d);
+  }
+  std::vector<int64_t> c = counts_at(ctx, n, b, ab_dev, ldab, pts);
+  const int64_t nu = c[0];
+  double dgood = 0.0;
+  for (size_t k = 0; k < ds.size(); ++k) {
+    if (c[1 + 2 * k] == nu && c[2 + 2 * k] == nu) {
+      dgood = ds[k];
+      break;
+    }
+  }
+  if (dgood == 0.0) fail(SP_EINVAL, "mu is (numerically) an eigenvalue: no gap found");
+  // refine between dgood and 2 dgood
+  pts.clear();
+  std::vector<double> lin;
+  for (int p = 1; p <= 127; ++p) {
+    const double d = dgood * (1.0 + p / 128.0);
+    lin.push_back(d);
+    pts.push_back(mu - d);
+    pts.push_back(mu + d);
+  }
+  c = counts_at(ctx, n, b, ab_dev, ldab, pts);
+  for (size_t p = 0; p < lin.size(); ++p) {
+    if (c[2 * p] == nu && c[2 * p + 1] == nu) dgood = lin[p];
+    else break;
+  }
+  *alpha = a;
+  *l0 = std::min(dgood / a, 1.0);
+}
+
+}  // namespace sp

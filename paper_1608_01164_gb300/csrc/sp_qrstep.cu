@@ -1,0 +1,471 @@
+// sp_qrstep.cu -- the QR-based first QDWH iteration (Sec. 4, Algorithms 1 and
+// 2, Remark "construct_off", Theorems 4 and 6).
+//
+// 1. Givens generation: the rotations of the fast QR of [s A; I] are produced
+//    in the algorithm's order by one warp that keeps a sliding window of the
+//    reduced matrix (top rows i..i+b, columns i..i+2b; the accumulator row
+//    n+1; bottom rows n+i..n+i+b-1).  Step i (1-based):
+//      alpha_{i,i}  rows (n+1, n+i)        alpha_{i,j}  rows (n+j, n+i), j < i+b
+//      beta_i       rows (i, n+1)          gamma_{i,j}  rows (i, j),     j <= i+b
+//    Rotation t acts on the ordered pair (p, q) as [[c, s], [-s, c]] with
+//    (c, s) = (f, g)/hypot(f, g), (f, g) = (R(p, col), R(q, col)), annihilating
+//    R(q, col).  This is a strictly sequential chain: latency-bound.
+// 2. Q1 = Q(1:n, 1:n), Q2 = Q(n+1:2n, 1:n) in HODLR format.  Every row of Q
+//    evolves independently under the rotations (they mix columns), so:
+//    * a leaf's rows are replayed from step lo+1-b to its last step, giving
+//      its dense diagonal blocks of Q1 and Q2, the b x b corner of Q1 left of
+//      it (Q1 is b-Hessenberg), and the values of the 2b "basis" columns
+//        hi+1..hi+b, n+1, n+hi+1..n+hi+b-1     (Theorem 6's span U)
+//      after its last step;
+//    * for a left child nu, the coefficients of Q's columns in nu's basis are
+//      rows of a 2b x (live columns) matrix that the same rotations act on;
+//      one thread per basis vector replays the sibling's steps, recording the
+//      coefficients of each sibling column when it becomes final (V_nu) and
+//      of the parent's basis columns at the end (E_nu);
+//    * the parent's basis restricted to the left child's rows is U_nu E_nu, to
+//      the right child's rows U_right (same basis columns), assembled
+//      bottom-up by batched GEMMs.
+//    Upper blocks of Q1 and Q2: U_nu V_nu^T (rank <= 2b).  Lower blocks of Q1:
+//    the b x b corner; of Q2: zero (Q2 is upper triangular).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "sp_internal.h"
+
+namespace sp {
+
+int64_t givens_count(int64_t n, int b) { return (2 * (int64_t)b + 1) * n - (int64_t)b * b - b; }
+
+namespace {
+
+constexpr int kMaxB = 32;
+
+__host__ __device__ __forceinline__ int64_t mn64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+// number of rotations in step i (1-based) of Algorithm 2
+__host__ __device__ inline int64_t step_rotations(int64_t n, int b, int64_t i) {
+  int64_t cnt = 1;  // beta_i
+  if (i >= 2) cnt += 1 + mn64(n - i, b - 1);  // alpha group
+  if (i < n) cnt += mn64(n - i, b);            // gamma group
+  return cnt;
+}
+
+// (c, s) with c f + s g = r = hypot(f, g) >= 0 and -s f + c g = 0
+__device__ __forceinline__ void make_rot(double f, double g, double& c, double& s) {
+  const double h = f * f + g * g;
+  if (h == 0.0) {
+    c = 1.0;
+    s = 0.0;
+  } else if (h > 1e-280 && h < 1e280) {
+    const double ri = rsqrt(h);
+    c = f * ri;
+    s = g * ri;
+  } else {
+    const double r = hypot(f, g);
+    c = f / r;
+    s = g / r;
+  }
+}
+
+// --------------------------------------------------------- Givens (warp) ----
+// 0-based step i <-> paper step i+1.  Live rows at step i: top rows i..i+b
+// (slot row % (b+1)), the accumulator row n (paper n+1, which starts as the
+// identity row e_1^T), bottom rows n+t, t in [i, i+b-1] (slot t % b).  Columns
+// are addressed by absolute index mod CW = 2b+2; the slot of a column is
+// cleared in every live row as soon as the column is finished, so it is zero
+// when it is reused for column + CW.
+__global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+                                                double mu, double scale, double* __restrict__ cs) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int CW = 2 * b + 2;
+  double* top = reinterpret_cast<double*>(smem_raw);
+  double* r1 = top + (b + 1) * CW;
+  double* bot = r1 + CW;
+  const int lane = threadIdx.x;
+  for (int e = lane; e < (2 * b + 2) * CW; e += 32) top[e] = 0.0;
+  __syncwarp();
+  // top row r of scale*(A - mu I): columns [r-b, r+b]
+  auto load_top = [&](int64_t r) {
+    double* T = top + (r % (b + 1)) * CW;
+    for (int64_t x = r - b + lane; x <= r + b; x += 32) {
+      if (x < 0 || x >= n) continue;
+      const int64_t d = r - x;
+      const int64_t dd = d < 0 ? -d : d;
+      double v = ab[dd + (d >= 0 ? x : r) * ldab];
+      if (d == 0) v -= mu;
+      T[x % CW] = scale * v;
+    }
+  };
+  for (int64_t r = 0; r <= b && r < n; ++r) load_top(r);
+  if (lane == 0) {
+    r1[0] = 1.0;
+    for (int64_t t = 1; t <= b && t < n; ++t) bot[(t % b) * CW + (t % CW)] = 1.0;
+  }
+  __syncwarp();
+  int64_t idx = 0;
+  // rotate window rows P (kept) and Q (annihilated in column col) over
+  // absolute columns [col, c_hi]
+  auto rot = [&](double* P, double* Q, int64_t col, int64_t c_lo, int64_t c_hi) {
+    const double f = P[col % CW], g = Q[col % CW];
+    double c, s;
+    make_rot(f, g, c, s);
+    __syncwarp();  // every lane has read (f, g) before any lane updates them
+    for (int64_t x = c_lo + lane; x <= c_hi; x += 32) {
+      const int sl = (int)(x % CW);
+      const double u = P[sl], v = Q[sl];
+      P[sl] = c * u + s * v;
+      Q[sl] = (x == col) ? 0.0 : -s * u + c * v;
+    }
+    if (lane == 0) {
+      cs[2 * idx] = c;
+      cs[2 * idx + 1] = s;
+    }
+    ++idx;
+    __syncwarp();
+  };
+  for (int64_t i = 0; i < n; ++i) {
+    double* Ti = top + (i % (b + 1)) * CW;
+    const int64_t chi = mn64(n - 1, i + 2 * b);
+    if (i >= 1) {
+      double* Bi = bot + (i % b) * CW;
+      const int64_t bhi = mn64(n - 1, i + b);
+      rot(r1, Bi, i, i, bhi);  // alpha_{i,i}
+      const int64_t jmax = mn64(n - 1, i + b - 1);
+      for (int64_t j = i + 1; j <= jmax; ++j) rot(bot + (j % b) * CW, Bi, j, i, bhi);  // alpha_{i,j}
+    }
+    rot(Ti, r1, i, i, chi);  // beta_i
+    const int64_t jg = mn64(n - 1, i + b);
+    for (int64_t j = i + 1; j <= jg; ++j) rot(Ti, top + (j % (b + 1)) * CW, i, i, chi);  // gamma_{i,j}
+    // column i is finished: clear its slot everywhere; retire top row i and
+    // bottom row n+i, bring in top row i+b+1 and bottom row n+i+b
+    const int ci = (int)(i % CW);
+    if (lane <= b) top[lane * CW + ci] = 0.0;
+    if (lane == 0) r1[ci] = 0.0;
+    if (lane < b) bot[lane * CW + ci] = 0.0;
+    for (int x = lane; x < CW; x += 32) Ti[x] = 0.0;
+    if (i >= 1)
+      for (int x = lane; x < CW; x += 32) bot[(i % b) * CW + x] = 0.0;
+    __syncwarp();
+    if (i + b + 1 < n) load_top(i + b + 1);
+    if (i >= 1 && lane == 0 && i + b < n) bot[(i % b) * CW + ((i + b) % CW)] = 1.0;
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ row replay ----
+// State of one row vector over the live columns of Q (or of one row of a
+// basis-coefficient matrix).  Top column x < n lives in slot x % (b+1),
+// bottom column n+t (t >= 1) in slot t % b, column n separately.  A column not
+// seen yet starts at its initial value: the unit vector's entry for Q rows,
+// zero for coefficient rows.
+struct RowState {
+  double tv[kMaxB + 1];
+  int64_t to[kMaxB + 1];
+  double bv[kMaxB];
+  int64_t bo[kMaxB];
+  double cn;
+  bool cn_live;
+  int64_t n;
+  int b;
+  int64_t myrow;  // global row of Q for Q rows, -1 for coefficient rows
+
+  __device__ void init(int64_t n_, int b_, int64_t row) {
+    n = n_;
+    b = b_;
+    myrow = row;
+    for (int k = 0; k <= b; ++k) to[k] = -1;
+    for (int k = 0; k < b; ++k) bo[k] = -1;
+    cn_live = false;
+  }
+  __device__ double init_val(int64_t col) const { return col == myrow ? 1.0 : 0.0; }
+  __device__ double& ref(int64_t col) {
+    if (col == n) {
+      if (!cn_live) {
+        cn = init_val(col);
+        cn_live = true;
+      }
+      return cn;
+    }
+    if (col < n) {
+      const int sl = (int)(col % (b + 1));
+      if (to[sl] != col) {
+        to[sl] = col;
+        tv[sl] = init_val(col);
+      }
+      return tv[sl];
+    }
+    const int sl = (int)((col - n) % b);
+    if (bo[sl] != col) {
+      bo[sl] = col;
+      bv[sl] = init_val(col);
+    }
+    return bv[sl];
+  }
+  __device__ double val(int64_t col) {
+    if (col < 0 || col >= 2 * n) return 0.0;
+    return ref(col);
+  }
+  __device__ void rotate(int64_t p, int64_t q, double c, double s) {
+    double& u = ref(p);
+    double& v = ref(q);
+    const double x = u, y = v;
+    u = c * x + s * y;
+    v = -s * x + c * y;
+  }
+};
+
+// basis column t of a node whose rows end (exclusive) at h:
+//   t < b: top column h+t; t = b: column n; t > b: bottom column n+h+(t-b-1)
+__device__ __forceinline__ int64_t basis_col(int64_t n, int b, int64_t h, int t) {
+  if (t < b) return (h + t < n) ? h + t : -1;
+  if (t == b) return n;
+  const int64_t bc = h + (t - b - 1);
+  return (bc < n) ? n + bc : -1;
+}
+
+// apply the rotations of 0-based step i to the row state
+__device__ __forceinline__ void replay_step(RowState& st, const double* __restrict__ cs,
+                                            const int64_t* __restrict__ off, int64_t i) {
+  const int64_t n = st.n;
+  const int b = st.b;
+  int64_t idx = off[i];
+  if (i >= 1) {
+    st.rotate(n, n + i, __ldg(cs + 2 * idx), __ldg(cs + 2 * idx + 1));
+    ++idx;
+    const int64_t jmax = min(n - 1, i + b - 1);
+    for (int64_t j = i + 1; j <= jmax; ++j, ++idx) st.rotate(n + j, n + i, __ldg(cs + 2 * idx), __ldg(cs + 2 * idx + 1));
+  }
+  st.rotate(i, n, __ldg(cs + 2 * idx), __ldg(cs + 2 * idx + 1));
+  ++idx;
+  const int64_t jg = min(n - 1, i + b);
+  for (int64_t j = i + 1; j <= jg; ++j, ++idx) st.rotate(i, j, __ldg(cs + 2 * idx), __ldg(cs + 2 * idx + 1));
+}
+
+struct LeafReplay {
+  int64_t lo;
+  int s;
+  double* q1;  // leaf slot of Q1 (ld)
+  double* q2;  // leaf slot of Q2
+  int ld;
+  double* corner;  // s x b (ld s), columns lo-b .. lo-1 of Q1 on the leaf rows
+  double* ub1;     // basis values on the top rows, ld n (pointer at row lo)
+  double* ub2;     // on the bottom rows
+};
+
+// one CTA per leaf, one thread per row of [Q1; Q2] restricted to the leaf
+__global__ void k_replay_leaf(const LeafReplay* __restrict__ jobs, const double* __restrict__ cs,
+                              const int64_t* __restrict__ off, int64_t n, int b) {
+  const LeafReplay jb = jobs[blockIdx.x];
+  const int r = threadIdx.x;
+  if (r >= 2 * jb.s) return;
+  const bool is_top = r < jb.s;
+  const int rr = is_top ? r : r - jb.s;
+  RowState st;
+  st.init(n, b, is_top ? jb.lo + rr : n + jb.lo + rr);
+  const int64_t hi = jb.lo + jb.s;
+  for (int64_t i = max((int64_t)0, jb.lo - b); i < hi; ++i) {
+    replay_step(st, cs, off, i);
+    const double v = st.val(i);
+    if (i >= jb.lo) {
+      if (is_top) jb.q1[rr + (int64_t)(i - jb.lo) * jb.ld] = v;
+      else jb.q2[rr + (int64_t)(i - jb.lo) * jb.ld] = v;
+    } else if (is_top) {
+      jb.corner[rr + (int64_t)(i - (jb.lo - b)) * jb.s] = v;
+    }
+  }
+  for (int t = 0; t < 2 * b; ++t) {
+    const int64_t col = basis_col(n, b, hi, t);
+    const double v = col < 0 ? 0.0 : st.val(col);
+    if (is_top) jb.ub1[rr + (int64_t)t * n] = v;
+    else jb.ub2[rr + (int64_t)t * n] = v;
+  }
+}
+
+struct TrackJob {
+  int64_t hi;   // end (exclusive) of the left child's rows
+  int64_t hi2;  // end of the sibling's rows
+  double* V;    // (hi2 - hi) x 2b, ld n: coefficients of the sibling columns
+  double* E;    // 2b x 2b (ld 2b): coefficients of the parent's basis columns
+};
+
+// one warp per left child, one lane per basis vector
+__global__ void k_replay_track(const TrackJob* __restrict__ jobs, int njobs, const double* __restrict__ cs,
+                               const int64_t* __restrict__ off, int64_t n, int b) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) / 64;
+  const int t = threadIdx.x % 64;
+  if (w >= njobs || t >= 2 * b) return;
+  const TrackJob jb = jobs[w];
+  RowState st;
+  st.init(n, b, -1);
+  for (int u = 0; u < 2 * b; ++u) {
+    const int64_t col = basis_col(n, b, jb.hi, u);
+    if (col >= 0) st.ref(col) = (u == t) ? 1.0 : 0.0;
+  }
+  for (int64_t i = jb.hi; i < jb.hi2; ++i) {
+    replay_step(st, cs, off, i);
+    jb.V[(i - jb.hi) + (int64_t)t * n] = st.val(i);
+  }
+  for (int u = 0; u < 2 * b; ++u) {
+    const int64_t col = basis_col(n, b, jb.hi2, u);
+    jb.E[t + (int64_t)u * 2 * b] = col < 0 ? 0.0 : st.val(col);
+  }
+}
+
+// right child c: U = b x b corner (first b rows), V = identity tail of the left
+// sibling (rows I_{c-1}), rank b; left child handled by basis GEMMs.
+__global__ void k_corner_blocks(const double* __restrict__ corner, int cs_ld, int64_t n, int b, int cap, double* U,
+                                double* V, int64_t lo_c, int s_c, int s_left, int* rank, int c) {
+  for (int64_t e = threadIdx.x; e < (int64_t)s_c * cap; e += blockDim.x) {
+    const int ii = (int)(e % s_c), t = (int)(e / s_c);
+    U[ii + (int64_t)t * n] = (ii < b && t < b) ? corner[ii + (int64_t)t * cs_ld] : 0.0;
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)s_left * cap; e += blockDim.x) {
+    const int jj = (int)(e % s_left), t = (int)(e / s_left);
+    V[jj + (int64_t)t * n] = (t < b && jj == s_left - b + t) ? 1.0 : 0.0;
+  }
+  if (threadIdx.x == 0) *rank = b;
+  (void)lo_c;
+  (void)c;
+}
+
+}  // namespace
+
+void givens_generate(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double scale,
+                     double* cs_dev) {
+  if (b < 1 || b > kMaxB) fail(SP_EINVAL, "bandwidth out of range for the fast QR step");
+  const size_t sm = sizeof(double) * (size_t)(2 * b + 2) * (2 * b + 2);
+  k_givens<<<1, 32, sm, ctx->stream>>>(ab_dev, ldab, n, b, mu, scale, cs_dev);
+  check_launch("k_givens");
+}
+
+static std::vector<int64_t> step_offsets(int64_t n, int b) {
+  std::vector<int64_t> off(n + 1);
+  off[0] = 0;
+  for (int64_t i = 0; i < n; ++i) off[i + 1] = off[i] + step_rotations(n, b, i + 1);
+  return off;
+}
+
+void fastqr_factors(sp_ctx* ctx, const sp_hodlr* A, double scale, sp_hodlr** Q1out, sp_hodlr** Q2out) {
+  const Tree& T = *A->tree;
+  const int64_t n = T.n;
+  const int b = A->b;
+  const int L = T.L;
+  if (!A->band) fail(SP_EINVAL, "fast QR step needs a handle built from a band");
+  if (2 * b > A->cap) fail(SP_EINVAL, "rank capacity below 2b");
+  if (b > kMaxB) fail(SP_EINVAL, "bandwidth above the fast QR limit");
+  if (2 * T.leaf_max > 1024) fail(SP_EINVAL, "leaf too large for the row replay (max 512)");
+  cudaStream_t st = ctx->stream;
+  const int64_t ng = givens_count(n, b);
+  DBuf csb((size_t)std::max<int64_t>(ng, 1) * 2 * sizeof(double), st);
+  givens_generate(ctx, n, b, A->band, b + 1, A->mu, scale, csb.as<double>());
+  DBuf offb = upload(step_offsets(n, b), st);
+  sp_hodlr* Q1 = hodlr_alloc(ctx, A->tree, A->cap, A->tol);
+  sp_hodlr* Q2 = nullptr;
+  try {
+    Q2 = hodlr_alloc(ctx, A->tree, A->cap, A->tol);
+    hodlr_set_zero(ctx, Q1);
+    hodlr_set_zero(ctx, Q2);
+    const int w2 = 2 * b;
+    const size_t lvl = (size_t)n * w2;
+    // basis arrays per level 1..L (top rows and bottom rows), tracker V per level
+    DBuf ub1((size_t)(L + 1) * lvl * sizeof(double) + 16, st), ub2((size_t)(L + 1) * lvl * sizeof(double) + 16, st);
+    DBuf vt((size_t)(L + 1) * lvl * sizeof(double) + 16, st);
+    DBuf eb((size_t)T.nodes() * w2 * w2 * sizeof(double) + 16, st);
+    DBuf cb((size_t)T.nleaves() * T.leaf_max * b * sizeof(double) + 16, st);
+    auto UB1 = [&](int l) { return ub1.as<double>() + (size_t)l * lvl; };
+    auto UB2 = [&](int l) { return ub2.as<double>() + (size_t)l * lvl; };
+    auto VT = [&](int l) { return vt.as<double>() + (size_t)l * lvl; };
+    auto EB = [&](int c) { return eb.as<double>() + (size_t)c * w2 * w2; };
+    auto CB = [&](int j) { return cb.as<double>() + (size_t)j * T.leaf_max * b; };
+    // leaves
+    std::vector<LeafReplay> lj;
+    for (int j = 0; j < T.nleaves(); ++j) {
+      const int c = (1 << L) + j;
+      lj.push_back(LeafReplay{T.lo[c], (int)T.sz[c], Q1->leaf(j), Q2->leaf(j), Q1->leaf_ld, CB(j),
+                              UB1(L) + T.lo[c], UB2(L) + T.lo[c]});
+    }
+    {
+      DBuf d = upload(lj, st);
+      const int threads = ((2 * T.leaf_max + 31) / 32) * 32;
+      k_replay_leaf<<<T.nleaves(), threads, 0, st>>>(d.as<LeafReplay>(), csb.as<double>(), offb.as<int64_t>(), n, b);
+      check_launch("k_replay_leaf");
+    }
+    if (L > 0) {
+      // trackers for every left child
+      std::vector<TrackJob> tj;
+      std::vector<int> tnode;
+      for (int c = 2; c < T.nodes(); c += 2) {
+        const int l = Tree::level_of(c);
+        tj.push_back(TrackJob{T.lo[c] + T.sz[c], T.lo[c + 1] + T.sz[c + 1], VT(l) + T.lo[c + 1], EB(c)});
+        tnode.push_back(c);
+      }
+      DBuf d = upload(tj, st);
+      const int nj = (int)tj.size();
+      const int per_block = 4;  // 4 jobs x 64 threads
+      k_replay_track<<<(nj + per_block - 1) / per_block, 64 * per_block, 0, st>>>(d.as<TrackJob>(), nj,
+                                                                                  csb.as<double>(),
+                                                                                  offb.as<int64_t>(), n, b);
+      check_launch("k_replay_track");
+      // bases bottom-up: U_parent(I_c) = U_c E_c (left child), U_parent(I_{c+1}) = U_{c+1}
+      for (int l = L; l >= 2; --l) {
+        std::vector<GemmTask> gtk;
+        for (int c = 1 << l; c < (2 << l); c += 2) {
+          gtk.push_back(gt(UB1(l) + T.lo[c], n, EB(c), w2, UB1(l - 1) + T.lo[c], n, (int)T.sz[c], w2, w2, 1.0, 0.0));
+          gtk.push_back(gt(UB2(l) + T.lo[c], n, EB(c), w2, UB2(l - 1) + T.lo[c], n, (int)T.sz[c], w2, w2, 1.0, 0.0));
+          check_cuda(cudaMemcpy2DAsync(UB1(l - 1) + T.lo[c + 1], n * sizeof(double), UB1(l) + T.lo[c + 1],
+                                       n * sizeof(double), T.sz[c + 1] * sizeof(double), w2,
+                                       cudaMemcpyDeviceToDevice, st),
+                     "basis copy");
+          check_cuda(cudaMemcpy2DAsync(UB2(l - 1) + T.lo[c + 1], n * sizeof(double), UB2(l) + T.lo[c + 1],
+                                       n * sizeof(double), T.sz[c + 1] * sizeof(double), w2,
+                                       cudaMemcpyDeviceToDevice, st),
+                     "basis copy");
+        }
+        gemm_batched(ctx, false, false, gtk);
+      }
+      // blocks
+      std::vector<int> ranks(T.nodes(), 0);
+      for (int c = 2; c < T.nodes(); ++c) {
+        const int l = Tree::level_of(c);
+        if ((c & 1) == 0) {
+          // upper block (rows I_c, cols I_{c+1}) of Q1 and Q2
+          for (int q = 0; q < 2; ++q) {
+            sp_hodlr* Q = q == 0 ? Q1 : Q2;
+            double* ubs = q == 0 ? UB1(l) : UB2(l);
+            check_cuda(cudaMemcpy2DAsync(Q->Uc(c), n * sizeof(double), ubs + T.lo[c], n * sizeof(double),
+                                         T.sz[c] * sizeof(double), w2, cudaMemcpyDeviceToDevice, st),
+                       "U copy");
+            check_cuda(cudaMemcpy2DAsync(Q->Vc(c), n * sizeof(double), VT(l) + T.lo[c + 1], n * sizeof(double),
+                                         T.sz[c + 1] * sizeof(double), w2, cudaMemcpyDeviceToDevice, st),
+                       "V copy");
+          }
+          ranks[c] = w2;
+        } else {
+          // lower block of Q1: b x b corner from the first leaf of c
+          const int j0 = (c << (L - l)) - (1 << L);
+          k_corner_blocks<<<1, 256, 0, st>>>(CB(j0), (int)T.sz[(1 << L) + j0], n, b, Q1->cap, Q1->Uc(c), Q1->Vc(c),
+                                             T.lo[c], (int)T.sz[c], (int)T.sz[c - 1], Q1->rank + c, c);
+          check_launch("k_corner_blocks");
+          ranks[c] = -1;  // set by the kernel (Q1) / zero (Q2)
+        }
+      }
+      std::vector<int> r1(T.nodes(), 0), r2(T.nodes(), 0);
+      for (int c = 2; c < T.nodes(); ++c) {
+        r1[c] = ranks[c] < 0 ? b : ranks[c];
+        r2[c] = ranks[c] < 0 ? 0 : ranks[c];
+      }
+      check_cuda(cudaMemcpyAsync(Q1->rank, r1.data(), sizeof(int) * r1.size(), cudaMemcpyHostToDevice, st), "ranks");
+      check_cuda(cudaMemcpyAsync(Q2->rank, r2.data(), sizeof(int) * r2.size(), cudaMemcpyHostToDevice, st), "ranks");
+      check_cuda(cudaStreamSynchronize(st), "sync");
+    }
+  } catch (...) {
+    hodlr_free(Q1);
+    hodlr_free(Q2);
+    throw;
+  }
+  *Q1out = Q1;
+  *Q2out = Q2;
+}
+
+}  // namespace sp
