@@ -92,6 +92,24 @@ const char* sp_last_error(sp_ctx_t ctx);
  * reports any sticky device error flag (rank overflow, breakdown, timeout). */
 int sp_ctx_sync(sp_ctx_t ctx);
 
+/* ---- measurement (not part of the method) ---- */
+
+/* Profiling switch: when on, every launch of a kernel family is bracketed by
+ * CUDA events on the context stream and the binary64 kernels count the
+ * floating-point operations they perform (from the actual, device-resident
+ * sizes) into device counters.  Turning it on or off resets the counters.
+ * Synchronising. */
+int sp_ctx_set_profiling(sp_ctx_t ctx, int on);
+/* Accumulated launches, elapsed milliseconds (sum of event pairs) and counted
+ * flops of kernel family `kernel` (0 <= kernel < sp_kernel_count()) since the
+ * last reset.  Synchronising. */
+int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, double* flops);
+/* Name of a kernel family ("k_gemm", "k_qr", ...), "" if out of range. */
+const char* sp_kernel_name(int kernel);
+int sp_kernel_count(void);
+/* Number of kernels this library has launched in the process so far. */
+int64_t sp_launch_count(void);
+
 /* HODLR representation of X_0 = A - mu I (Sec. 3.1.1): the index set is split
  * by balanced bisection into 2^L leaves of at most `leaf` indices (L the
  * smallest depth with ceil(n / 2^L) <= leaf); leaves are dense and every

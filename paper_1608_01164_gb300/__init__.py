@@ -32,7 +32,8 @@ EXPORTS = [
     "sp_hodlr_from_band", "sp_qdwh_sign", "sp_projector", "sp_apply", "sp_to_dense", "sp_trace",
     "sp_hodlr_info", "sp_hodlr_destroy", "sp_hodlr_add", "sp_hodlr_mult", "sp_hodlr_cholesky",
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
-    "sp_fastqr_factors",
+    "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_kernel_name", "sp_kernel_count",
+    "sp_launch_count",
 ]
 
 
@@ -112,6 +113,11 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_qdwh_start": (I, [P, I64, I32, P, I64, D, ctypes.POINTER(D), ctypes.POINTER(D)]),
         "sp_givens_generate": (I, [P, I64, I32, P, I64, D, P]),
         "sp_fastqr_factors": (I, [P, P, D, PP, PP]),
+        "sp_ctx_set_profiling": (I, [P, I]),
+        "sp_ctx_profile": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "sp_kernel_name": (ctypes.c_char_p, [I]),
+        "sp_kernel_count": (I, []),
+        "sp_launch_count": (I64, []),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -287,3 +293,21 @@ def sp_fastqr_factors(ctx, A, scale: float):
     q1, q2 = ctypes.c_void_p(), ctypes.c_void_p()
     _check(ctx, _lib.sp_fastqr_factors(ctx, A, float(scale), ctypes.byref(q1), ctypes.byref(q2)))
     return q1, q2
+
+
+def sp_ctx_set_profiling(ctx, on: bool):
+    _check(ctx, _lib.sp_ctx_set_profiling(ctx, int(bool(on))))
+
+
+def sp_ctx_profile(ctx):
+    """{kernel name: (launches, ms, flops)} for every kernel family."""
+    out = {}
+    for k in range(_lib.sp_kernel_count()):
+        la, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        _check(ctx, _lib.sp_ctx_profile(ctx, k, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(fl)))
+        out[_lib.sp_kernel_name(k).decode()] = (la.value, ms.value, fl.value)
+    return out
+
+
+def sp_launch_count() -> int:
+    return int(_lib.sp_launch_count())

@@ -129,16 +129,23 @@ struct Timer {
   }
 };
 
-// one Cholesky-based QDWH step: X <- (b/c) X + (a - b/c) Z^{-1} X, Z = I + c X^2
+// one Cholesky-based QDWH step: X <- (b/c) X + (a - b/c) Z^{-1} X, Z = I + c X^2,
+// with Z = L L^T and Z^{-1} X = L^{-T} (L^{-1} X) as two formatted products with
+// the HODLR inverse factor built during the factorisation.
 sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c) {
   Owned Z(hodlr_mult(ctx, X, X));
   hodlr_scale_shift(ctx, Z.p, c, 1.0);
-  Owned Lf(hodlr_cholesky(ctx, Z.p));
+  sp_hodlr *lf = nullptr, *li = nullptr;
+  hodlr_cholesky_inv(ctx, Z.p, &lf, &li);
+  Owned Lf(lf), Li(li);
   Z.reset(nullptr);
-  Owned Y(hodlr_trsm(ctx, Lf.p, false, X));
-  Owned V(hodlr_trsm(ctx, Lf.p, true, Y.p));
-  Y.reset(nullptr);
   Lf.reset(nullptr);
+  Owned Y(hodlr_mult(ctx, Li.p, X));
+  Owned LiT(hodlr_transpose(ctx, Li.p));
+  Li.reset(nullptr);
+  Owned V(hodlr_mult(ctx, LiT.p, Y.p));
+  Y.reset(nullptr);
+  LiT.reset(nullptr);
   Owned Xn(hodlr_add(ctx, b / c, X, a - b / c, V.p, 0.0));
   V.reset(nullptr);
   hodlr_symmetrize(ctx, Xn.p);
@@ -202,6 +209,12 @@ void sp_ctx_destroy(sp_ctx_t ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
   if (ctx->d_flags) cudaFree(ctx->d_flags);
+  if (ctx->d_fc) cudaFree(ctx->d_fc);
+  for (int k = 0; k < KID_COUNT; ++k)
+    for (auto& e : ctx->ev[k]) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
   delete ctx;
 }
 
@@ -211,6 +224,58 @@ int sp_ctx_sync(sp_ctx_t ctx) {
   if (!ctx) return SP_EINVAL;
   return guarded(ctx, [&] { check_flags(ctx, "enqueued work"); });
 }
+
+int sp_ctx_set_profiling(sp_ctx_t ctx, int on) {
+  if (!ctx) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    if (!ctx->d_fc) check_cuda(cudaMalloc(&ctx->d_fc, sizeof(double) * KID_COUNT), "profiler counters");
+    check_cuda(cudaMemset(ctx->d_fc, 0, sizeof(double) * KID_COUNT), "profiler counters");
+    for (int k = 0; k < KID_COUNT; ++k) {
+      for (auto& e : ctx->ev[k]) {
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+      ctx->ev[k].clear();
+      ctx->launches[k] = 0;
+      ctx->ms[k] = 0.0;
+    }
+    ctx->profiling = on != 0;
+  });
+}
+
+int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, double* flops) {
+  if (!ctx || kernel < 0 || kernel >= KID_COUNT) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    for (int k = 0; k < KID_COUNT; ++k) {
+      for (auto& e : ctx->ev[k]) {
+        float t = 0.f;
+        check_cuda(cudaEventElapsedTime(&t, e.first, e.second), "event time");
+        ctx->ms[k] += t;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+      }
+      ctx->ev[k].clear();
+    }
+    double h[KID_COUNT] = {};
+    if (ctx->d_fc) check_cuda(cudaMemcpy(h, ctx->d_fc, sizeof(h), cudaMemcpyDeviceToHost), "profiler counters");
+    if (launches) *launches = ctx->launches[kernel];
+    if (ms) *ms = ctx->ms[kernel];
+    if (flops) *flops = h[kernel];
+  });
+}
+
+const char* sp_kernel_name(int kernel) {
+  static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_jacobi_svd", "k_gather",
+                                         "k_leaf_potrf", "k_leaf_trsm", "k_givens", "k_replay_leaf",
+                                         "k_replay_track", "k_inertia", "misc"};
+  return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
+}
+
+int sp_kernel_count(void) { return KID_COUNT; }
+
+int64_t sp_launch_count(void) { return launch_count(); }
 
 int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, int32_t leaf,
                        double tol, int32_t rank_cap, sp_hodlr_t* out) {
@@ -363,7 +428,7 @@ void sp_hodlr_destroy(sp_hodlr_t M) { hodlr_free(M); }
 
 int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr_t B, double gamma, sp_hodlr_t* C) {
   if (!ctx || !A || !C) return SP_EINVAL;
-  if (B && B->tree != A->tree) return SP_EINVAL;
+  if (B && !same_tree(*B->tree, *A->tree)) return SP_EINVAL;
   return guarded(ctx, [&] {
     *C = hodlr_add(ctx, alpha, A, beta, B, gamma);
     check_flags(ctx, "sp_hodlr_add");
@@ -371,7 +436,7 @@ int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr
 }
 
 int sp_hodlr_mult(sp_ctx_t ctx, sp_hodlr_t A, sp_hodlr_t B, sp_hodlr_t* C) {
-  if (!ctx || !A || !B || !C || A->tree != B->tree) return SP_EINVAL;
+  if (!ctx || !A || !B || !C || !same_tree(*A->tree, *B->tree)) return SP_EINVAL;
   return guarded(ctx, [&] {
     *C = hodlr_mult(ctx, A, B);
     check_flags(ctx, "sp_hodlr_mult");
@@ -393,7 +458,7 @@ int sp_hodlr_cholesky(sp_ctx_t ctx, sp_hodlr_t Z, sp_hodlr_t* L) {
 }
 
 int sp_hodlr_trsm(sp_ctx_t ctx, sp_hodlr_t L, int trans, sp_hodlr_t B, sp_hodlr_t* X) {
-  if (!ctx || !L || !B || !X || L->tree != B->tree) return SP_EINVAL;
+  if (!ctx || !L || !B || !X || !same_tree(*L->tree, *B->tree)) return SP_EINVAL;
   return guarded(ctx, [&] {
     *X = hodlr_trsm(ctx, L, trans != 0, B);
     check_flags(ctx, "sp_hodlr_trsm");

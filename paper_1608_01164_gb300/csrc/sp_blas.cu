@@ -8,6 +8,7 @@
 // FP64 pipe (ridge ~0.18 flop/byte); the tiling aims at keeping each SM's
 // DFMA pipe busy, not at saving bytes.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <stdexcept>
 
@@ -22,7 +23,33 @@ void check_cuda(cudaError_t e, const char* what) {
   if (e != cudaSuccess) fail(SP_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-void check_launch(const char* what) { check_cuda(cudaGetLastError(), what); }
+namespace {
+std::atomic<int64_t> g_launches{0};
+}
+
+void check_launch(const char* what) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  check_cuda(cudaGetLastError(), what);
+}
+
+int64_t launch_count() { return g_launches.load(); }
+
+ProfScope::ProfScope(sp_ctx* c, int k) : ctx(c), kid(k) {
+  if (ctx->profiling) {
+    cudaEventCreate(&a);
+    cudaEventRecord(a, ctx->stream);
+  }
+}
+
+ProfScope::~ProfScope() {
+  if (ctx->profiling && a) {
+    cudaEvent_t b = nullptr;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, ctx->stream);
+    ctx->ev[kid].emplace_back(a, b);
+    ctx->launches[kid] += 1;
+  }
+}
 
 // ------------------------------------------------------------------ memory --
 void* dmalloc(size_t bytes, cudaStream_t st) {
@@ -58,7 +85,8 @@ __device__ __forceinline__ int dsize(int s, const int* p) {
 }
 
 template <bool TA, bool TB>
-__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int atomic) {
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int atomic,
+                                              double* fc) {
   const GemmTask t = tasks[blockIdx.y];
   const int m = dsize(t.m, t.pm), n = dsize(t.n, t.pn), k = dsize(t.k, t.pk);
   const int tiles_m = (m + kGT - 1) / kGT;
@@ -120,6 +148,8 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
         else *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
       }
     }
+  if (fc && threadIdx.x == 0)
+    atomicAdd(fc, 2.0 * (double)min(kGT, m - row0) * (double)min(kGT, n - col0) * (double)max(kend - kbeg, 0));
 }
 
 __global__ void k_axpby(const AxpbyTask* __restrict__ tasks) {
@@ -270,10 +300,12 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     DBuf d = upload(part, ctx->stream);
     dim3 grid(maxtiles, (unsigned)cnt, nz);
     const GemmTask* dt = d.as<GemmTask>();
-    if (!ta && !tb) k_gemm<false, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0);
-    else if (ta && !tb) k_gemm<true, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0);
-    else if (!ta && tb) k_gemm<false, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0);
-    else k_gemm<true, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0);
+    double* fc = fc_ptr(ctx, KID_GEMM);
+    ProfScope ps(ctx, KID_GEMM);
+    if (!ta && !tb) k_gemm<false, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
+    else if (ta && !tb) k_gemm<true, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
+    else if (!ta && tb) k_gemm<false, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
+    else k_gemm<true, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
     check_launch("k_gemm");
   }
 }
@@ -310,6 +342,7 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   if (tasks.empty()) return;
   for (const auto& t : tasks) ctx->flops += (double)t.n * t.n * t.n / 3.0;
   DBuf d = upload(tasks, ctx->stream);
+  ProfScope ps(ctx, KID_POTRF);
   k_leaf_potrf<<<(unsigned)tasks.size(), 256, 0, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags);
   check_launch("k_leaf_potrf");
 }
@@ -326,6 +359,7 @@ void leaf_trsm(sp_ctx* ctx, bool trans, const std::vector<LeafTask>& tasks) {
     std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
     DBuf d = upload(part, ctx->stream);
     dim3 grid((maxw + 63) / 64, (unsigned)cnt);
+    ProfScope ps(ctx, KID_TRSM);
     if (trans) k_leaf_trsm<true><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
     else k_leaf_trsm<false><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
     check_launch("k_leaf_trsm");

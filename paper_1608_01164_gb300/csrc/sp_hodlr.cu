@@ -106,7 +106,7 @@ void hodlr_set_zero(sp_ctx* ctx, sp_hodlr* M) {
 }
 
 void hodlr_copy(sp_ctx* ctx, const sp_hodlr* S, sp_hodlr* D) {
-  if (S->cap != D->cap || S->tree != D->tree) fail(SP_EINTERNAL, "hodlr_copy shape mismatch");
+  if (S->cap != D->cap || !same_tree(*S->tree, *D->tree)) fail(SP_EINTERNAL, "hodlr_copy shape mismatch");
   const size_t nl = (size_t)S->tree->nleaves() * S->leaf_ld * S->leaf_ld;
   const size_t nf = (size_t)std::max(S->L(), 1) * S->n() * S->cap;
   check_cuda(cudaMemcpyAsync(D->leaves, S->leaves, nl * sizeof(double), cudaMemcpyDeviceToDevice, ctx->stream), "cp");
@@ -542,7 +542,7 @@ void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M) {
 
 // ---------------------------------------------------------------- product ---
 sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
-  if (A->tree != B->tree) fail(SP_EINVAL, "hodlr_mult: operands on different trees");
+  if (!same_tree(*A->tree, *B->tree)) fail(SP_EINVAL, "hodlr_mult: operands on different trees");
   const Tree& T = *A->tree;
   const int L = T.L;
   const int cap = std::max(A->cap, B->cap);
@@ -671,54 +671,96 @@ static void lr_update_sub(sp_ctx* ctx, sp_hodlr* M, int c, const double* Ul, int
   gemm_batched(ctx, false, true, lt);
 }
 
-// ---------------------------------------------------- skinny solves ---------
-// X(I_c) <- L_c^{-1} X (trans = false) or L_c^{-T} X (trans = true) for the
-// lower-triangular HODLR factor L; X: |I_c| x w (pointer at row lo[c]).
-static void trsm_skinny(sp_ctx* ctx, const sp_hodlr* Lf, int c, double* X, int64_t ldx, int w, const int* pw,
-                        bool trans, double* tmp) {
+// ------------------------------------------------------- leaf inverses ------
+// Li_leaf = L_leaf^{-1} for lower-triangular leaves (identity, then a leaf
+// forward substitution with n right-hand sides).
+static void leaf_inverse(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* Li, const std::vector<int>& leaves) {
   const Tree& T = *Lf->tree;
-  if (Tree::level_of(c) == T.L) {
+  std::vector<AxpbyTask> id;
+  std::vector<LeafTask> tr;
+  for (int c : leaves) {
     const int jl = c - (1 << T.L);
-    leaf_trsm(ctx, trans, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], X, ldx, w, pw}});
-    return;
+    const int s = (int)T.sz[c];
+    id.push_back(AxpbyTask{nullptr, Li->leaf(jl), 0, Li->leaf_ld, Li->leaf_ld, Li->leaf_ld, nullptr, nullptr, 0.0,
+                           0.0, 1.0});
+    tr.push_back(LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, Li->leaf(jl), Li->leaf_ld, s, nullptr});
   }
-  const int c1 = 2 * c, c2 = 2 * c + 1;
-  double* X1 = X;
-  double* X2 = X + (T.lo[c2] - T.lo[c]);
-  // L21 = B_{c2} = U_{c2} V_{c2}^T (rows I_c2, cols I_c1)
-  if (!trans) {
-    trsm_skinny(ctx, Lf, c1, X1, ldx, w, pw, false, tmp);
-    // X2 -= U_{c2} (V_{c2}^T X1)
-    gemm_batched(ctx, true, false,
-                 {gt(Lf->Vc(c2), T.n, X1, ldx, tmp, Lf->cap, Lf->cap, w, (int)T.sz[c1], 1.0, 0.0, Lf->rank + c2, pw)});
-    gemm_batched(ctx, false, false,
-                 {gt(Lf->Uc(c2), T.n, tmp, Lf->cap, X2, ldx, (int)T.sz[c2], w, Lf->cap, -1.0, 1.0, nullptr, pw,
-                     Lf->rank + c2)});
-    trsm_skinny(ctx, Lf, c2, X2, ldx, w, pw, false, tmp);
-  } else {
-    trsm_skinny(ctx, Lf, c2, X2, ldx, w, pw, true, tmp);
-    // X1 -= L21^T X2 = V_{c2} (U_{c2}^T X2)
-    gemm_batched(ctx, true, false,
-                 {gt(Lf->Uc(c2), T.n, X2, ldx, tmp, Lf->cap, Lf->cap, w, (int)T.sz[c2], 1.0, 0.0, Lf->rank + c2, pw)});
-    gemm_batched(ctx, false, false,
-                 {gt(Lf->Vc(c2), T.n, tmp, Lf->cap, X1, ldx, (int)T.sz[c1], w, Lf->cap, -1.0, 1.0, nullptr, pw,
-                     Lf->rank + c2)});
-    trsm_skinny(ctx, Lf, c1, X1, ldx, w, pw, true, tmp);
+  axpby_batched(ctx, id);
+  leaf_trsm(ctx, false, tr);
+}
+
+// Lower block of the inverse at the right child c2 of a factored node:
+// (L^{-1})_{21} = -L22^{-1} L21 L11^{-1} = -(L22^{-1} U)(L11^{-T} V)^T with
+// L21 = U V^T, the same rank as L21 (exact, no recompression).  `roots2` are
+// right children, their left siblings are the c1's; both subtrees of Li must
+// already hold their inverses.
+static void inverse_blocks(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* Li, const std::vector<int>& roots2) {
+  if (roots2.empty()) return;
+  const Tree& T = *Lf->tree;
+  const int l = Tree::level_of(roots2[0]);
+  std::vector<int> roots1;
+  for (int c2 : roots2) roots1.push_back(c2 ^ 1);
+  // U side: rows I_c2 of level l: Li_sub(c2) U_c2, width rank[c2]
+  apply_roots(ctx, Li, roots2, Lf->Ul(l), T.n, Li->Ul(l), T.n, Lf->cap, Lf->rank, false, false, false);
+  // V side: rows I_c1 hold V_c2: Li_sub(c1)^T V_c2, width rank[c1 ^ 1]
+  apply_roots(ctx, Li, roots1, Lf->Vl(l), T.n, Li->Vl(l), T.n, Lf->cap, Lf->rank, true, true, false);
+  std::vector<AxpbyTask> neg;
+  std::vector<ZeroTailTask> zt;
+  for (int c2 : roots2) {
+    const int c1 = c2 ^ 1;
+    neg.push_back(AxpbyTask{nullptr, Li->Uc(c2), 0, T.n, (int)T.sz[c2], Lf->cap, nullptr, nullptr, 0.0, -1.0, 0.0});
+    check_cuda(cudaMemcpyAsync(Li->rank + c2, Lf->rank + c2, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream),
+               "rank copy");
+    check_cuda(cudaMemsetAsync(Li->rank + c1, 0, sizeof(int), ctx->stream), "rank zero");
+    zt.push_back(ZeroTailTask{Li->Uc(c1), T.n, (int)T.sz[c1], Li->rank + c1, Lf->cap});
+    zt.push_back(ZeroTailTask{Li->Vc(c1), T.n, (int)T.sz[c2], Li->rank + c1, Lf->cap});
   }
+  axpby_batched(ctx, neg);
+  zero_tail_batched(ctx, zt);
+}
+
+// Level-parallel inverse of a lower-triangular HODLR factor: leaves first,
+// then bottom-up, each level's blocks from the inverses of their children.
+sp_hodlr* hodlr_tri_inverse(sp_ctx* ctx, const sp_hodlr* Lf) {
+  const Tree& T = *Lf->tree;
+  sp_hodlr* Li = hodlr_alloc(ctx, Lf->tree, Lf->cap, Lf->tol);
+  try {
+    hodlr_set_zero(ctx, Li);
+    std::vector<int> leaves;
+    for (int c = 1 << T.L; c < (2 << T.L); ++c) leaves.push_back(c);
+    leaf_inverse(ctx, Lf, Li, leaves);
+    for (int l = T.L; l >= 1; --l) {
+      std::vector<int> r2;
+      for (int c = (1 << l) + 1; c < (2 << l); c += 2) r2.push_back(c);
+      inverse_blocks(ctx, Lf, Li, r2);
+    }
+  } catch (...) {
+    hodlr_free(Li);
+    throw;
+  }
+  return Li;
 }
 
 // ------------------------------------------------------------- H-Cholesky ---
-static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, int c, double* tmp, double* G, double* UG) {
+// Recursive factorisation Z = L L^T (left subtree, Schur complement of the
+// right subtree, right subtree), carrying the inverse factor Li = L^{-1}
+// along so that every triangular solve with a factored subtree is a parallel
+// HODLR-times-skinny product instead of a chain of leaf substitutions.
+static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, sp_hodlr* Li, int c, double* tmp, double* G, double* UG) {
   const Tree& T = *Lf->tree;
   if (Tree::level_of(c) == T.L) {
     const int jl = c - (1 << T.L);
     leaf_potrf(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], nullptr, 0, 0, nullptr}});
+    leaf_inverse(ctx, Lf, Li, {c});
     return;
   }
   const int c1 = 2 * c, c2 = 2 * c + 1;
-  chol_rec(ctx, Lf, c1, tmp, G, UG);
-  // L21 = Z21 L11^{-T}: V_{c2} <- L11^{-1} V_{c2}
-  trsm_skinny(ctx, Lf, c1, Lf->Vc(c2), T.n, Lf->cap, Lf->rank + c2, false, tmp);
+  chol_rec(ctx, Lf, Li, c1, tmp, G, UG);
+  // L21 = Z21 L11^{-T} = U (L11^{-1} V)^T: V_{c2} <- Li_sub(c1) V_{c2}
+  hodlr_apply_sub(ctx, Li, c1, Lf->Vc(c2), T.n, tmp, T.sz[c1], Lf->cap, Lf->rank + c2, false, false);
+  check_cuda(cudaMemcpy2DAsync(Lf->Vc(c2), T.n * sizeof(double), tmp, T.sz[c1] * sizeof(double),
+                               T.sz[c1] * sizeof(double), Lf->cap, cudaMemcpyDeviceToDevice, ctx->stream),
+             "V copy");
   // Schur complement: Z22 -= U (V^T V) U^T
   gemm_batched(ctx, true, false,
                {gt(Lf->Vc(c2), T.n, Lf->Vc(c2), T.n, G, Lf->cap, Lf->cap, Lf->cap, (int)T.sz[c1], 1.0, 0.0,
@@ -732,133 +774,57 @@ static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, int c, double* tmp, double* G, d
   check_launch("k_set_int");
   zero_tail_batched(ctx, {ZeroTailTask{Lf->Uc(c1), T.n, (int)T.sz[c1], Lf->rank + c1, Lf->cap},
                           ZeroTailTask{Lf->Vc(c1), T.n, (int)T.sz[c2], Lf->rank + c1, Lf->cap}});
-  chol_rec(ctx, Lf, c2, tmp, G, UG);
+  chol_rec(ctx, Lf, Li, c2, tmp, G, UG);
+  inverse_blocks(ctx, Lf, Li, {c2});
+}
+
+void hodlr_cholesky_inv(sp_ctx* ctx, const sp_hodlr* Z, sp_hodlr** Lout, sp_hodlr** Liout) {
+  sp_hodlr* Lf = hodlr_alloc(ctx, Z->tree, Z->cap, Z->tol);
+  sp_hodlr* Li = nullptr;
+  try {
+    Li = hodlr_alloc(ctx, Z->tree, Z->cap, Z->tol);
+    hodlr_copy(ctx, Z, Lf);
+    hodlr_set_zero(ctx, Li);
+    const Tree& T = *Z->tree;
+    DBuf tmp((size_t)(T.n / 2 + 1) * Z->cap * sizeof(double) + 16, ctx->stream);
+    DBuf G((size_t)Z->cap * Z->cap * sizeof(double) + 16, ctx->stream);
+    DBuf UG((size_t)(T.n / 2 + 1) * Z->cap * sizeof(double) + 16, ctx->stream);
+    chol_rec(ctx, Lf, Li, 1, tmp.as<double>(), G.as<double>(), UG.as<double>());
+  } catch (...) {
+    hodlr_free(Lf);
+    hodlr_free(Li);
+    throw;
+  }
+  *Lout = Lf;
+  *Liout = Li;
 }
 
 sp_hodlr* hodlr_cholesky(sp_ctx* ctx, const sp_hodlr* Z) {
-  sp_hodlr* Lf = hodlr_alloc(ctx, Z->tree, Z->cap, Z->tol);
-  try {
-    hodlr_copy(ctx, Z, Lf);
-    const Tree& T = *Z->tree;
-    DBuf tmp((size_t)Z->cap * Z->cap * sizeof(double) + 16, ctx->stream);
-    DBuf G((size_t)Z->cap * Z->cap * sizeof(double) + 16, ctx->stream);
-    DBuf UG((size_t)(T.n / 2 + 1) * Z->cap * sizeof(double) + 16, ctx->stream);
-    chol_rec(ctx, Lf, 1, tmp.as<double>(), G.as<double>(), UG.as<double>());
-  } catch (...) {
-    hodlr_free(Lf);
-    throw;
-  }
+  sp_hodlr *Lf = nullptr, *Li = nullptr;
+  hodlr_cholesky_inv(ctx, Z, &Lf, &Li);
+  hodlr_free(Li);
   return Lf;
 }
 
 // --------------------------------------------- triangular solve, HODLR RHS --
-struct SolveWs {
-  double* tmp;   // cap x cap
-  double* P;     // n x cap
-  double* K;     // cap x cap
-  double* Ul;    // n x cap
-};
-
-// X_sub(c) <- L_c^{-1} X_sub(c)
-static void solve_rec(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* X, int c, SolveWs& ws) {
-  const Tree& T = *Lf->tree;
-  if (Tree::level_of(c) == T.L) {
-    const int jl = c - (1 << T.L);
-    const int s = (int)T.sz[c];
-    leaf_trsm(ctx, false, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, X->leaf(jl), X->leaf_ld, s, nullptr}});
-    return;
-  }
-  const int c1 = 2 * c, c2 = 2 * c + 1;
-  const int cap = X->cap, capL = Lf->cap;
-  solve_rec(ctx, Lf, X, c1, ws);
-  // X12 = L11^{-1} B12: U_{c1} <- L11^{-1} U_{c1}
-  trsm_skinny(ctx, Lf, c1, X->Uc(c1), T.n, cap, X->rank + c1, false, ws.tmp);
-  // X21 = L22^{-1} (B21 - L21 X11):  L21 X11 = U^L_{c2} (X11^T V^L_{c2})^T
-  hodlr_apply_sub(ctx, X, c1, Lf->Vc(c2), T.n, ws.P, T.sz[c1], capL, Lf->rank + c2, true, false);
-  {
-    LrBlock lb;
-    lb.m = (int)T.sz[c2];
-    lb.q = (int)T.sz[c1];
-    lb.segs.push_back(Seg{X->Uc(c2), X->Vc(c2), T.n, T.n, cap, X->rank + c2, 1.0});
-    lb.segs.push_back(Seg{Lf->Uc(c2), ws.P, T.n, T.sz[c1], capL, Lf->rank + c2, -1.0});
-    lb.Uout = X->Uc(c2);
-    lb.Vout = X->Vc(c2);
-    lb.ldu_out = lb.ldv_out = T.n;
-    lb.rank_out = X->rank + c2;
-    lb.cap = cap;
-    recompress(ctx, {lb}, X->tol);
-  }
-  trsm_skinny(ctx, Lf, c2, X->Uc(c2), T.n, cap, X->rank + c2, false, ws.tmp);
-  // X22 <- B22 - L21 X12 = B22 - U^L_{c2} (V^L_{c2}^T U^X_{c1}) V^X_{c1}^T
-  gemm_batched(ctx, true, false,
-               {gt(Lf->Vc(c2), T.n, X->Uc(c1), T.n, ws.K, capL, capL, cap, (int)T.sz[c1], 1.0, 0.0, Lf->rank + c2,
-                   X->rank + c1)});
-  gemm_batched(ctx, false, false,
-               {gt(Lf->Uc(c2), T.n, ws.K, capL, ws.Ul, T.sz[c2], (int)T.sz[c2], cap, capL, 1.0, 0.0, nullptr,
-                   X->rank + c1, Lf->rank + c2)});
-  lr_update_sub(ctx, X, c2, ws.Ul, T.sz[c2], X->Vc(c1), T.n, cap, X->rank + c1, -1.0);
-  solve_rec(ctx, Lf, X, c2, ws);
-}
-
-// X_sub(c) <- L_c^{-T} X_sub(c)
-static void solveT_rec(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* X, int c, SolveWs& ws) {
-  const Tree& T = *Lf->tree;
-  if (Tree::level_of(c) == T.L) {
-    const int jl = c - (1 << T.L);
-    const int s = (int)T.sz[c];
-    leaf_trsm(ctx, true, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, X->leaf(jl), X->leaf_ld, s, nullptr}});
-    return;
-  }
-  const int c1 = 2 * c, c2 = 2 * c + 1;
-  const int cap = X->cap, capL = Lf->cap;
-  solveT_rec(ctx, Lf, X, c2, ws);
-  // X21 = L22^{-T} B21: U_{c2} <- L22^{-T} U_{c2}
-  trsm_skinny(ctx, Lf, c2, X->Uc(c2), T.n, cap, X->rank + c2, true, ws.tmp);
-  // X12 = L11^{-T} (B12 - L21^T X22), L21^T X22 = V^L_{c2} (X22^T U^L_{c2})^T
-  hodlr_apply_sub(ctx, X, c2, Lf->Uc(c2), T.n, ws.P, T.sz[c2], capL, Lf->rank + c2, true, false);
-  {
-    LrBlock lb;
-    lb.m = (int)T.sz[c1];
-    lb.q = (int)T.sz[c2];
-    lb.segs.push_back(Seg{X->Uc(c1), X->Vc(c1), T.n, T.n, cap, X->rank + c1, 1.0});
-    lb.segs.push_back(Seg{Lf->Vc(c2), ws.P, T.n, T.sz[c2], capL, Lf->rank + c2, -1.0});
-    lb.Uout = X->Uc(c1);
-    lb.Vout = X->Vc(c1);
-    lb.ldu_out = lb.ldv_out = T.n;
-    lb.rank_out = X->rank + c1;
-    lb.cap = cap;
-    recompress(ctx, {lb}, X->tol);
-  }
-  trsm_skinny(ctx, Lf, c1, X->Uc(c1), T.n, cap, X->rank + c1, true, ws.tmp);
-  // X11 <- B11 - L21^T X21 = B11 - V^L_{c2} (U^L_{c2}^T U^X_{c2}) V^X_{c2}^T
-  gemm_batched(ctx, true, false,
-               {gt(Lf->Uc(c2), T.n, X->Uc(c2), T.n, ws.K, capL, capL, cap, (int)T.sz[c2], 1.0, 0.0, Lf->rank + c2,
-                   X->rank + c2)});
-  gemm_batched(ctx, false, false,
-               {gt(Lf->Vc(c2), T.n, ws.K, capL, ws.Ul, T.sz[c1], (int)T.sz[c1], cap, capL, 1.0, 0.0, nullptr,
-                   X->rank + c2, Lf->rank + c2)});
-  lr_update_sub(ctx, X, c1, ws.Ul, T.sz[c1], X->Vc(c2), T.n, cap, X->rank + c2, -1.0);
-  solveT_rec(ctx, Lf, X, c1, ws);
-}
-
+// X = op(L)^{-1} B as the formatted product op(L^{-1}) *_H B with the HODLR
+// inverse of the triangular factor (level-parallel, see hodlr_tri_inverse).
 sp_hodlr* hodlr_trsm(sp_ctx* ctx, const sp_hodlr* Lf, bool trans, const sp_hodlr* B) {
-  if (Lf->tree != B->tree) fail(SP_EINVAL, "hodlr_trsm: operands on different trees");
-  sp_hodlr* X = hodlr_alloc(ctx, B->tree, B->cap, B->tol);
+  if (!same_tree(*Lf->tree, *B->tree)) fail(SP_EINVAL, "hodlr_trsm: operands on different trees");
+  sp_hodlr* Li = hodlr_tri_inverse(ctx, Lf);
+  sp_hodlr* X = nullptr;
   try {
-    hodlr_copy(ctx, B, X);
-    const Tree& T = *B->tree;
-    const int cm = std::max(B->cap, Lf->cap);
-    DBuf tmp((size_t)cm * cm * sizeof(double) + 16, ctx->stream);
-    DBuf P((size_t)(T.n / 2 + 1) * cm * sizeof(double) + 16, ctx->stream);
-    DBuf K((size_t)cm * cm * sizeof(double) + 16, ctx->stream);
-    DBuf Ul((size_t)(T.n / 2 + 1) * cm * sizeof(double) + 16, ctx->stream);
-    SolveWs ws{tmp.as<double>(), P.as<double>(), K.as<double>(), Ul.as<double>()};
-    if (!trans) solve_rec(ctx, Lf, X, 1, ws);
-    else solveT_rec(ctx, Lf, X, 1, ws);
+    if (trans) {
+      sp_hodlr* LiT = hodlr_transpose(ctx, Li);
+      hodlr_free(Li);
+      Li = LiT;
+    }
+    X = hodlr_mult(ctx, Li, B);
   } catch (...) {
-    hodlr_free(X);
+    hodlr_free(Li);
     throw;
   }
+  hodlr_free(Li);
   return X;
 }
 

@@ -41,6 +41,8 @@ struct Tree {
 };
 
 std::shared_ptr<Tree> make_tree(int64_t n, int leaf);
+// Two HODLR matrices can be combined when their partitions coincide.
+inline bool same_tree(const Tree& a, const Tree& b) { return a.n == b.n && a.L == b.L && a.lo == b.lo; }
 
 }  // namespace sp
 
@@ -68,6 +70,14 @@ struct sp_hodlr {
   double* Vc(int c) const { return Vl(sp::Tree::level_of(c)) + tree->lo[c ^ 1]; }
 };
 
+namespace sp {
+// Kernel families timed and flop-counted by the profiler.
+enum KernelId {
+  KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_JACOBI, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
+  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_COUNT
+};
+}  // namespace sp
+
 struct sp_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
@@ -75,6 +85,13 @@ struct sp_ctx {
   std::string err;
   int* d_flags = nullptr;  // [0] rank overflow, [1] breakdown, [2] non-finite, [3] timeout
   double flops = 0.0;      // nominal flops of enqueued task lists
+  // profiler: CUDA events around every launch of a kernel family, and the
+  // algorithmic flops the kernels count themselves (d_fc[kid])
+  bool profiling = false;
+  double* d_fc = nullptr;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
+  int64_t launches[sp::KID_COUNT] = {};
+  double ms[sp::KID_COUNT] = {};
 };
 
 namespace sp {
@@ -89,6 +106,20 @@ struct Error {
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 void check_launch(const char* what);
+
+// Process-wide count of kernel launches made by the library.
+int64_t launch_count();
+
+// Brackets one launch of a kernel family with CUDA events when profiling.
+struct ProfScope {
+  sp_ctx* ctx;
+  int kid;
+  cudaEvent_t a = nullptr;
+  ProfScope(sp_ctx* c, int k);
+  ~ProfScope();
+};
+// Device flop counter of a family (null unless profiling).
+inline double* fc_ptr(sp_ctx* ctx, int kid) { return ctx->profiling ? ctx->d_fc + kid : nullptr; }
 
 // ------------------------------------------------------------------ memory --
 // Stream-ordered device buffer (freed on the context stream when destroyed).
@@ -230,6 +261,9 @@ double hodlr_trace(sp_ctx* ctx, const sp_hodlr* M);
 sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma);
 sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B);
 sp_hodlr* hodlr_cholesky(sp_ctx* ctx, const sp_hodlr* Z);
+// H-Cholesky returning both the factor L and its HODLR inverse L^{-1}.
+void hodlr_cholesky_inv(sp_ctx* ctx, const sp_hodlr* Z, sp_hodlr** L, sp_hodlr** Li);
+sp_hodlr* hodlr_tri_inverse(sp_ctx* ctx, const sp_hodlr* L);
 sp_hodlr* hodlr_trsm(sp_ctx* ctx, const sp_hodlr* L, bool trans, const sp_hodlr* B);
 void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M);
 sp_hodlr* hodlr_transpose(sp_ctx* ctx, const sp_hodlr* M);

@@ -26,6 +26,9 @@
 namespace sp {
 namespace {
 
+// shared memory available to the SVD kernel's working set (bytes)
+constexpr size_t kSvdSmemMax = 200 * 1024;
+
 __device__ __forceinline__ int dwidth(int w, const int* p) {
   if (!p) return w;
   int v = *p;
@@ -94,7 +97,7 @@ struct QrJob {
   int64_t ld_dst;
 };
 
-__global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs, double* fc) {
   const QrJob jb = jobs[blockIdx.x];
   const int R = dwidth(jb.Rmax, jb.pR);
   const int rows = jb.rows;
@@ -151,6 +154,12 @@ __global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs) {
     }
     __syncthreads();
   }
+  if (fc && threadIdx.x == 0) {
+    // per reflector j: norm (2 flops/row) + dot and axpy on R-j-1 columns (4 flops/row each)
+    double f = 0.0;
+    for (int j = 0; j < nref; ++j) f += (double)(rows - j) * (2.0 + 4.0 * (R - j - 1));
+    atomicAdd(fc, f);
+  }
   // copy R (nref x R upper trapezoid) into the Rmax x Rmax slot
   for (int64_t e = threadIdx.x; e < (int64_t)jb.Rmax * jb.Rmax; e += blockDim.x) {
     const int i = (int)(e % jb.Rmax), c = (int)(e / jb.Rmax);
@@ -178,7 +187,7 @@ struct ApplyJob {
   int cap;
 };
 
-__global__ void __launch_bounds__(256) k_apply_q(const ApplyJob* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) k_apply_q(const ApplyJob* __restrict__ jobs, double* fc) {
   const ApplyJob jb = jobs[blockIdx.x];
   const int R = dwidth(jb.Rmax, jb.pR);
   const int rows = jb.rows;
@@ -196,6 +205,11 @@ __global__ void __launch_bounds__(256) k_apply_q(const ApplyJob* __restrict__ jo
   __syncthreads();
   const double* J = jb.J;
   const int64_t ld = jb.ldj;
+  if (fc && threadIdx.x == 0) {
+    double f = 0.0;
+    for (int j = 0; j < nref; ++j) f += 4.0 * (double)(rows - j) * k;
+    atomicAdd(fc, f);
+  }
   for (int j = nref - 1; j >= 0; --j) {
     const double tau = jb.tau[j];
     if (tau != 0.0) {
@@ -238,77 +252,108 @@ __device__ __forceinline__ void rr_pair(int round, int p, int P, int& i, int& j)
   }
 }
 
-__global__ void __launch_bounds__(256) k_jacobi_svd(const SvdJob* __restrict__ jobs, double tol, int* flags) {
+// One CTA (32 warps) per core.  When rows*cols + cols*cols doubles fit in
+// shared memory (SMEM = true) the working matrix G and the accumulated right
+// rotations V live there; otherwise in the global work buffers.  Each round of
+// the round-robin ordering has P/2 disjoint column pairs, processed by the
+// warps concurrently (one warp per pair: three dot products, then the
+// rotation of both columns of G and V).
+template <bool SMEM>
+__global__ void __launch_bounds__(1024) k_jacobi_svd(const SvdJob* __restrict__ jobs, double tol, int* flags,
+                                                     double* fc) {
   const SvdJob jb = jobs[blockIdx.x];
   const int ru = *jb.pru, rv = *jb.prv;
   const bool tr = rv > ru;
   const int rows = tr ? rv : ru, cols = tr ? ru : rv;
-  const int ld = jb.Rmax;
-  double* G = jb.G;
-  double* V = jb.Vacc;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* sig = reinterpret_cast<double*>(smem_raw);
   int* perm = reinterpret_cast<int*>(sig + jb.Rmax);
+  double* G;
+  double* V;
+  int ldg, ldv;
+  if (SMEM) {
+    G = sig + jb.Rmax + (jb.Rmax + 1) / 2;  // after sig (Rmax doubles) and perm (Rmax ints)
+    V = G + (size_t)rows * cols;
+    ldg = rows;
+    ldv = cols;
+  } else {
+    G = jb.G;
+    V = jb.Vacc;
+    ldg = jb.Rmax;
+    ldv = jb.Rmax;
+  }
   __shared__ int s_rot;
   __shared__ int s_k;
+  const int ldm = jb.Rmax;
   for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
     const int i = (int)(e % rows), c = (int)(e / rows);
-    G[i + (int64_t)c * ld] = tr ? jb.M[c + (int64_t)i * ld] : jb.M[i + (int64_t)c * ld];
+    G[i + (int64_t)c * ldg] = tr ? jb.M[c + (int64_t)i * ldm] : jb.M[i + (int64_t)c * ldm];
   }
   for (int64_t e = threadIdx.x; e < (int64_t)cols * cols; e += blockDim.x) {
     const int i = (int)(e % cols), c = (int)(e / cols);
-    V[i + (int64_t)c * ld] = (i == c) ? 1.0 : 0.0;
+    V[i + (int64_t)c * ldv] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
   const int P = cols + (cols & 1);
   const double eps = 1e-15;
+  double nflop = 0.0;
   for (int sweep = 0; sweep < 60 && cols > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
+    int rotated = 0;
     for (int round = 0; round < P - 1; ++round) {
       for (int p = warp; p < P / 2; p += nw) {
         int i, j;
         rr_pair(round, p, P, i, j);
         if (i >= cols || j >= cols) continue;
+        double* gi = G + (int64_t)i * ldg;
+        double* gj = G + (int64_t)j * ldg;
         double a = 0.0, b = 0.0, g = 0.0;
         for (int r = lane; r < rows; r += 32) {
-          const double x = G[r + (int64_t)i * ld], y = G[r + (int64_t)j * ld];
-          a += x * x;
-          b += y * y;
-          g += x * y;
+          const double x = gi[r], y = gj[r];
+          a = fma(x, x, a);
+          b = fma(y, y, b);
+          g = fma(x, y, g);
         }
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
+        nflop += 6.0 * rows;
         if (g != 0.0 && fabs(g) > eps * sqrt(a * b)) {
+          nflop += 6.0 * rows + 6.0 * cols;
           const double zeta = (b - a) / (2.0 * g);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = 1.0 / sqrt(1.0 + t * t), sn = cs * t;
+          const double cs = rsqrt(1.0 + t * t), sn = cs * t;
           for (int r = lane; r < rows; r += 32) {
-            const double x = G[r + (int64_t)i * ld], y = G[r + (int64_t)j * ld];
-            G[r + (int64_t)i * ld] = cs * x - sn * y;
-            G[r + (int64_t)j * ld] = sn * x + cs * y;
+            const double x = gi[r], y = gj[r];
+            gi[r] = cs * x - sn * y;
+            gj[r] = sn * x + cs * y;
           }
+          double* vi = V + (int64_t)i * ldv;
+          double* vj = V + (int64_t)j * ldv;
           for (int r = lane; r < cols; r += 32) {
-            const double x = V[r + (int64_t)i * ld], y = V[r + (int64_t)j * ld];
-            V[r + (int64_t)i * ld] = cs * x - sn * y;
-            V[r + (int64_t)j * ld] = sn * x + cs * y;
+            const double x = vi[r], y = vj[r];
+            vi[r] = cs * x - sn * y;
+            vj[r] = sn * x + cs * y;
           }
-          if (lane == 0) s_rot = 1;
+          rotated = 1;
         }
       }
       __syncthreads();
     }
+    if (rotated && lane == 0) s_rot = 1;
+    __syncthreads();
     if (!s_rot) break;
     __syncthreads();
   }
+  if (fc && lane == 0 && nflop > 0.0) atomicAdd(fc, nflop);
   // singular values = column norms
   for (int c = warp; c < cols; c += nw) {
     double a = 0.0;
     for (int r = lane; r < rows; r += 32) {
-      const double x = G[r + (int64_t)c * ld];
-      a += x * x;
+      const double x = G[r + (int64_t)c * ldg];
+      a = fma(x, x, a);
     }
     a = warp_sum(a);
     if (lane == 0) sig[c] = sqrt(a);
@@ -332,6 +377,7 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdJob* __restrict__ j
   }
   __syncthreads();
   const int k = s_k;
+  const int ld = jb.Rmax;
   for (int64_t e = threadIdx.x; e < (int64_t)ld * jb.cap; e += blockDim.x) {
     const int r = (int)(e % ld), p = (int)(e / ld);
     double u = 0.0, v = 0.0;
@@ -339,11 +385,11 @@ __global__ void __launch_bounds__(256) k_jacobi_svd(const SvdJob* __restrict__ j
       const int c = perm[p];
       const double s = sig[c];
       if (!tr) {
-        if (r < ru) u = G[r + (int64_t)c * ld];
-        if (r < rv) v = V[r + (int64_t)c * ld];
+        if (r < ru) u = G[r + (int64_t)c * ldg];
+        if (r < rv) v = V[r + (int64_t)c * ldv];
       } else {
-        if (r < ru) u = V[r + (int64_t)c * ld] * s;
-        if (r < rv) v = (s > 0.0) ? G[r + (int64_t)c * ld] / s : 0.0;
+        if (r < ru) u = V[r + (int64_t)c * ldv] * s;
+        if (r < rv) v = (s > 0.0) ? G[r + (int64_t)c * ldg] / s : 0.0;
       }
     }
     jb.SU[r + (int64_t)p * ld] = u;
@@ -532,6 +578,7 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     for (int off = 0; off < nb; off += 65535) {
       const int cnt = std::min(65535, nb - off);
       dim3 grid((maxrows + 255) / 256, maxseg, cnt);
+      ProfScope ps(ctx, KID_GATHER);
       k_gather<<<grid, 256, 0, st>>>(dgb.as<GatherBlock>() + off, dseg.as<Seg>(), maxseg);
       check_launch("k_gather");
     }
@@ -540,26 +587,57 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
   for (auto& lvl : qrl) {
     if (lvl.empty()) continue;
     DBuf d = upload(lvl, st);
-    k_qr<<<(unsigned)lvl.size(), 256, 0, st>>>(d.as<QrJob>());
+    ProfScope ps(ctx, KID_QR);
+    k_qr<<<(unsigned)lvl.size(), 256, 0, st>>>(d.as<QrJob>(), fc_ptr(ctx, KID_QR));
     check_launch("k_qr");
   }
   // 3. cores
   gemm_batched(ctx, false, true, core);
-  // 4. SVD + truncation
+  // 4. SVD + truncation: cores whose working set fits in shared memory take
+  // the shared-memory kernel, the rest the global-memory one
   {
-    DBuf d = upload(svd, st);
-    const size_t sm = (size_t)maxR * (sizeof(double) + sizeof(int)) + 64;
-    if (sm > 48 * 1024)
-      check_cuda(cudaFuncSetAttribute(k_jacobi_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+    std::vector<SvdJob> small, large;
+    int maxR_small = 1, maxR_large = 1;
+    size_t need_small = 0;
+    for (int t = 0; t < nb; ++t) {
+      const size_t R = (size_t)Rmax[t];
+      const size_t bytes = R * (sizeof(double) + sizeof(int)) + 2 * R * R * sizeof(double) + 64;
+      if (bytes <= kSvdSmemMax) {
+        small.push_back(svd[t]);
+        maxR_small = std::max(maxR_small, Rmax[t]);
+        need_small = std::max(need_small, bytes);
+      } else {
+        large.push_back(svd[t]);
+        maxR_large = std::max(maxR_large, Rmax[t]);
+      }
+    }
+    ProfScope ps(ctx, KID_JACOBI);
+    if (!small.empty()) {
+      DBuf d = upload(small, st);
+      check_cuda(cudaFuncSetAttribute(k_jacobi_svd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kSvdSmemMax),
                  "smem attr");
-    k_jacobi_svd<<<(unsigned)nb, 256, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags);
-    check_launch("k_jacobi_svd");
+      k_jacobi_svd<true><<<(unsigned)small.size(), 1024, need_small, st>>>(d.as<SvdJob>(), tol, ctx->d_flags,
+                                                                            fc_ptr(ctx, KID_JACOBI));
+      check_launch("k_jacobi_svd");
+    }
+    if (!large.empty()) {
+      DBuf d = upload(large, st);
+      const size_t sm = (size_t)maxR_large * (sizeof(double) + sizeof(int)) + 64;
+      if (sm > 48 * 1024)
+        check_cuda(cudaFuncSetAttribute(k_jacobi_svd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                   "smem attr");
+      k_jacobi_svd<false><<<(unsigned)large.size(), 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags,
+                                                                     fc_ptr(ctx, KID_JACOBI));
+      check_launch("k_jacobi_svd");
+    }
   }
   // 5. apply reflectors top-down
   for (auto& lvl : apl) {
     if (lvl.empty()) continue;
     DBuf d = upload(lvl, st);
-    k_apply_q<<<(unsigned)lvl.size(), 256, 0, st>>>(d.as<ApplyJob>());
+    ProfScope ps(ctx, KID_APPLYQ);
+    k_apply_q<<<(unsigned)lvl.size(), 256, 0, st>>>(d.as<ApplyJob>(), fc_ptr(ctx, KID_APPLYQ));
     check_launch("k_apply_q");
   }
 }

@@ -112,6 +112,7 @@ void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t
   for (double v : h) amax = std::max(amax, v);
   const double pivmin = DBL_MIN * amax * amax;
   DBuf ring(b > 1 ? (size_t)nshift * (b * b + b) * sizeof(double) : 16, ctx->stream);
+  ProfScope ps(ctx, KID_INERTIA);
   k_inertia<<<(nshift + 63) / 64, 64, 0, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev, pivmin,
                                                         ring.as<double>());
   check_launch("k_inertia");

@@ -335,6 +335,7 @@ void givens_generate(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_
                      double* cs_dev) {
   if (b < 1 || b > kMaxB) fail(SP_EINVAL, "bandwidth out of range for the fast QR step");
   const size_t sm = sizeof(double) * (size_t)(2 * b + 2) * (2 * b + 2);
+  ProfScope ps(ctx, KID_GIVENS);
   k_givens<<<1, 32, sm, ctx->stream>>>(ab_dev, ldab, n, b, mu, scale, cs_dev);
   check_launch("k_givens");
 }
@@ -388,6 +389,7 @@ void fastqr_factors(sp_ctx* ctx, const sp_hodlr* A, double scale, sp_hodlr** Q1o
     {
       DBuf d = upload(lj, st);
       const int threads = ((2 * T.leaf_max + 31) / 32) * 32;
+      ProfScope ps(ctx, KID_REPLAY_LEAF);
       k_replay_leaf<<<T.nleaves(), threads, 0, st>>>(d.as<LeafReplay>(), csb.as<double>(), offb.as<int64_t>(), n, b);
       check_launch("k_replay_leaf");
     }
@@ -403,6 +405,7 @@ void fastqr_factors(sp_ctx* ctx, const sp_hodlr* A, double scale, sp_hodlr** Q1o
       DBuf d = upload(tj, st);
       const int nj = (int)tj.size();
       const int per_block = 4;  // 4 jobs x 64 threads
+      ProfScope ps(ctx, KID_REPLAY_TRACK);
       k_replay_track<<<(nj + per_block - 1) / per_block, 64 * per_block, 0, st>>>(d.as<TrackJob>(), nj,
                                                                                   csb.as<double>(),
                                                                                   offb.as<int64_t>(), n, b);
