@@ -77,6 +77,10 @@ typedef struct {
   size_t bytes;            /* device bytes held by the result */
   double ms_param, ms_qr, ms_chol, ms_total; /* phase times (CUDA events) */
   double flops;            /* nominal binary64 flops counted by the kernels' task lists */
+  /* inside the Cholesky-based steps: formatted products, H-Cholesky (with the
+   * inverse factor), the two products with the inverse factor, and the final
+   * combination + symmetrisation (CUDA events, summed over iterations) */
+  double ms_mult, ms_factor, ms_solve, ms_combine;
 } sp_info;
 
 /* Returns opts filled with the defaults listed above. */

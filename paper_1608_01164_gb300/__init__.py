@@ -54,7 +54,9 @@ class sp_info(ctypes.Structure):
                 ("l", ctypes.c_double * 16), ("a", ctypes.c_double * 16), ("b", ctypes.c_double * 16),
                 ("c", ctypes.c_double * 16), ("kind", ctypes.c_int * 16), ("max_rank", ctypes.c_int),
                 ("bytes", ctypes.c_size_t), ("ms_param", ctypes.c_double), ("ms_qr", ctypes.c_double),
-                ("ms_chol", ctypes.c_double), ("ms_total", ctypes.c_double), ("flops", ctypes.c_double)]
+                ("ms_chol", ctypes.c_double), ("ms_total", ctypes.c_double), ("flops", ctypes.c_double),
+                ("ms_mult", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
+                ("ms_combine", ctypes.c_double)]
 
 
 def build(force: bool = False, jobs: int = 6) -> str:

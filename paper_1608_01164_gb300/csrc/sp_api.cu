@@ -132,23 +132,31 @@ struct Timer {
 // one Cholesky-based QDWH step: X <- (b/c) X + (a - b/c) Z^{-1} X, Z = I + c X^2,
 // with Z = L L^T and Z^{-1} X = L^{-T} (L^{-1} X) as two formatted products with
 // the HODLR inverse factor built during the factorisation.
-sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c) {
+sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c, sp_info* inf) {
+  Timer t1(ctx->stream);
   Owned Z(hodlr_mult(ctx, X, X));
   hodlr_scale_shift(ctx, Z.p, c, 1.0);
+  inf->ms_mult += t1.stop();
+  Timer t2(ctx->stream);
   sp_hodlr *lf = nullptr, *li = nullptr;
   hodlr_cholesky_inv(ctx, Z.p, &lf, &li);
   Owned Lf(lf), Li(li);
   Z.reset(nullptr);
   Lf.reset(nullptr);
+  inf->ms_factor += t2.stop();
+  Timer t3(ctx->stream);
   Owned Y(hodlr_mult(ctx, Li.p, X));
   Owned LiT(hodlr_transpose(ctx, Li.p));
   Li.reset(nullptr);
   Owned V(hodlr_mult(ctx, LiT.p, Y.p));
   Y.reset(nullptr);
   LiT.reset(nullptr);
+  inf->ms_solve += t3.stop();
+  Timer t4(ctx->stream);
   Owned Xn(hodlr_add(ctx, b / c, X, a - b / c, V.p, 0.0));
   V.reset(nullptr);
   hodlr_symmetrize(ctx, Xn.p);
+  inf->ms_combine += t4.stop();
   return Xn.release();
 }
 
@@ -269,7 +277,8 @@ int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, doub
 const char* sp_kernel_name(int kernel) {
   static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_jacobi_svd", "k_gather",
                                          "k_leaf_potrf", "k_leaf_trsm", "k_givens", "k_replay_leaf",
-                                         "k_replay_track", "k_inertia", "misc"};
+                                         "k_replay_track", "k_inertia", "misc", "k_gemm[apply]",
+                                         "k_gemm[chol]", "k_gemm[mult]"};
   return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
 }
 
@@ -357,7 +366,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
         if (!X.p) {
           X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
         }
-        X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k]));
+        X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k], &inf));
         inf.kind[k] = 2;
         check_flags(ctx, "Cholesky-based step");
         inf.ms_chol += t.stop();

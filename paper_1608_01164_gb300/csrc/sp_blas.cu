@@ -177,43 +177,76 @@ __global__ void k_zero_tail(const ZeroTailTask* __restrict__ tasks) {
   }
 }
 
-// Right-looking unblocked Cholesky of one leaf per CTA (in global memory,
-// L2-resident: a leaf is at most 512 x 512 doubles).
-__global__ void __launch_bounds__(256) k_leaf_potrf(const LeafTask* __restrict__ tasks, int* flags) {
+// Blocked right-looking Cholesky of one leaf per CTA (1024 threads): each
+// 32-column panel (rows jb..n-1) is factored in shared memory, written back,
+// and the trailing lower triangle gets A22 -= P P^T, every thread producing
+// 2x2 outputs from the shared-memory panel.  The upper triangle is zeroed.
+constexpr int kPW = 32;  // panel width
+
+__global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict__ tasks, int* flags) {
   const LeafTask t = tasks[blockIdx.x];
   double* A = t.A;
   const int64_t lda = t.lda;
   const int n = t.n;
-  __shared__ double s_inv;
-  for (int j = 0; j < n; ++j) {
-    if (threadIdx.x == 0) {
-      double d = A[j + (int64_t)j * lda];
-      if (!(d > 0.0)) {
-        atomicOr(&flags[FLAG_BREAKDOWN], 1);
-        d = 1.0;
-      }
-      const double p = sqrt(d);
-      A[j + (int64_t)j * lda] = p;
-      s_inv = 1.0 / p;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* P = reinterpret_cast<double*>(smem_raw);  // panel, row-major (n rows x (kPW+1))
+  constexpr int LDP = kPW + 1;
+  for (int jb = 0; jb < n; jb += kPW) {
+    const int w = min(kPW, n - jb);
+    const int pr = n - jb;  // panel rows
+    for (int e = threadIdx.x; e < pr * w; e += blockDim.x) {
+      const int r = e % pr, c = e / pr;
+      P[r * LDP + c] = A[(jb + r) + (int64_t)(jb + c) * lda];
     }
     __syncthreads();
-    const double inv = s_inv;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[i + (int64_t)j * lda] *= inv;
-    __syncthreads();
-    // trailing update of the lower triangle: A(i,c) -= A(i,j) A(c,j), j < c <= i
-    const int m = n - j - 1;
-    const int64_t tri = (int64_t)m * (m + 1) / 2;
-    for (int64_t e = threadIdx.x; e < tri; e += blockDim.x) {
-      // column-major lower-triangle enumeration: column cc (0-based in the
-      // trailing block) holds m - cc entries
-      int cc = (int)((2.0 * m + 1.0 - sqrt((2.0 * m + 1.0) * (2.0 * m + 1.0) - 8.0 * (double)e)) * 0.5);
-      if (cc < 0) cc = 0;
-      while (cc > 0 && (int64_t)cc * (2 * m - cc + 1) / 2 > e) --cc;
-      while ((int64_t)(cc + 1) * (2 * m - cc) / 2 <= e) ++cc;
-      const int64_t start = (int64_t)cc * (2 * m - cc + 1) / 2;
-      const int ii = cc + (int)(e - start);
-      const int col = j + 1 + cc, row = j + 1 + ii;
-      A[row + (int64_t)col * lda] -= A[row + (int64_t)j * lda] * A[col + (int64_t)j * lda];
+    for (int j = 0; j < w; ++j) {
+      if (threadIdx.x == 0) {
+        double d = P[j * LDP + j];
+        if (!(d > 0.0)) {
+          atomicOr(&flags[FLAG_BREAKDOWN], 1);
+          d = 1.0;
+        }
+        P[j * LDP + j] = sqrt(d);
+      }
+      __syncthreads();
+      const double inv = 1.0 / P[j * LDP + j];
+      for (int r = j + 1 + threadIdx.x; r < pr; r += blockDim.x) P[r * LDP + j] *= inv;
+      __syncthreads();
+      // update panel columns j+1..w-1, rows >= column
+      const int nc = w - j - 1;
+      for (int e = threadIdx.x; e < (pr - j - 1) * nc; e += blockDim.x) {
+        const int r = j + 1 + e / nc, c = j + 1 + e % nc;
+        if (r >= c) P[r * LDP + c] -= P[r * LDP + j] * P[c * LDP + j];
+      }
+      __syncthreads();
+    }
+    for (int e = threadIdx.x; e < pr * w; e += blockDim.x) {
+      const int r = e % pr, c = e / pr;
+      A[(jb + r) + (int64_t)(jb + c) * lda] = (r >= c) ? P[r * LDP + c] : 0.0;
+    }
+    // trailing update: rows/cols jb+w..n-1, lower triangle, 2x2 per thread
+    const int m = n - jb - w;
+    const int mb = (m + 1) / 2;
+    for (int e = threadIdx.x; e < mb * mb; e += blockDim.x) {
+      const int bi = e % mb, bc = e / mb;
+      if (bi < bc) continue;
+      const int r0 = w + 2 * bi, c0 = w + 2 * bc;  // panel-relative rows
+      double a00 = 0.0, a01 = 0.0, a10 = 0.0, a11 = 0.0;
+      const bool r1ok = r0 + 1 < pr, c1ok = c0 + 1 < pr;
+#pragma unroll 8
+      for (int k = 0; k < w; ++k) {
+        const double x0 = P[r0 * LDP + k], y0 = P[c0 * LDP + k];
+        const double x1 = r1ok ? P[(r0 + 1) * LDP + k] : 0.0, y1 = c1ok ? P[(c0 + 1) * LDP + k] : 0.0;
+        a00 = fma(x0, y0, a00);
+        a01 = fma(x0, y1, a01);
+        a10 = fma(x1, y0, a10);
+        a11 = fma(x1, y1, a11);
+      }
+      const int64_t R0 = jb + r0, C0 = jb + c0;
+      A[R0 + C0 * lda] -= a00;
+      if (c1ok && r0 >= c0 + 1) A[R0 + (C0 + 1) * lda] -= a01;
+      if (r1ok) A[(R0 + 1) + C0 * lda] -= a10;
+      if (r1ok && c1ok) A[(R0 + 1) + (C0 + 1) * lda] -= a11;
     }
     __syncthreads();
   }
@@ -300,8 +333,8 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     DBuf d = upload(part, ctx->stream);
     dim3 grid(maxtiles, (unsigned)cnt, nz);
     const GemmTask* dt = d.as<GemmTask>();
-    double* fc = fc_ptr(ctx, KID_GEMM);
-    ProfScope ps(ctx, KID_GEMM);
+    double* fc = fc_ptr(ctx, ctx->gemm_kid);
+    ProfScope ps(ctx, ctx->gemm_kid);
     if (!ta && !tb) k_gemm<false, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
     else if (ta && !tb) k_gemm<true, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
     else if (!ta && tb) k_gemm<false, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
@@ -342,8 +375,13 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   if (tasks.empty()) return;
   for (const auto& t : tasks) ctx->flops += (double)t.n * t.n * t.n / 3.0;
   DBuf d = upload(tasks, ctx->stream);
+  int nmax = 1;
+  for (const auto& t : tasks) nmax = std::max(nmax, t.n);
+  const size_t sm = (size_t)nmax * (kPW + 1) * sizeof(double);
+  if (sm > 48 * 1024)
+    check_cuda(cudaFuncSetAttribute(k_leaf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "smem");
   ProfScope ps(ctx, KID_POTRF);
-  k_leaf_potrf<<<(unsigned)tasks.size(), 256, 0, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags);
+  k_leaf_potrf<<<(unsigned)tasks.size(), 1024, sm, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags);
   check_launch("k_leaf_potrf");
 }
 

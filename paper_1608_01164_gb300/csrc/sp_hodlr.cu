@@ -340,6 +340,7 @@ static void apply_roots(sp_ctx* ctx, const sp_hodlr* M, const std::vector<int>& 
   const Tree& T = *M->tree;
   const int L = T.L;
   const int rlev = Tree::level_of(roots[0]);
+  GemmSite site(ctx, ctx->gemm_kid == KID_GEMM_CHOL ? KID_GEMM_CHOL : KID_GEMM_APPLY);
   auto width_ptr = [&](int node_at_rlev) -> const int* {
     if (!pw_node) return nullptr;
     return pw_node + (pw_sib ? (node_at_rlev ^ 1) : node_at_rlev);
@@ -582,8 +583,11 @@ sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
       wt.push_back(gt(A->Uc(a), T.n, Ta, A->cap, Wl(l) + T.lo[a], T.n, (int)T.sz[a], B->cap, A->cap, 1.0, 0.0,
                       nullptr, B->rank + s, A->rank + a));
     }
-    gemm_batched(ctx, true, false, tt);
-    gemm_batched(ctx, false, false, wt);
+    {
+      GemmSite site(ctx, KID_GEMM_MULT);
+      gemm_batched(ctx, true, false, tt);
+      gemm_batched(ctx, false, false, wt);
+    }
     // off-diagonal blocks of C
     std::vector<LrBlock> blocks;
     for (int c = 2; c < T.nodes(); ++c) {
@@ -607,6 +611,7 @@ sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
     }
     recompress(ctx, blocks, C->tol);
     // leaves: A_leaf B_leaf + sum_l W_l(I_c) V^B_l(I_c)^T
+    GemmSite site(ctx, KID_GEMM_MULT);
     std::vector<GemmTask> lt;
     for (int j = 0; j < T.nleaves(); ++j) {
       const int c = (1 << L) + j;
@@ -755,6 +760,7 @@ static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, sp_hodlr* Li, int c, double* tmp
     return;
   }
   const int c1 = 2 * c, c2 = 2 * c + 1;
+  GemmSite site(ctx, KID_GEMM_CHOL);
   chol_rec(ctx, Lf, Li, c1, tmp, G, UG);
   // L21 = Z21 L11^{-T} = U (L11^{-1} V)^T: V_{c2} <- Li_sub(c1) V_{c2}
   hodlr_apply_sub(ctx, Li, c1, Lf->Vc(c2), T.n, tmp, T.sz[c1], Lf->cap, Lf->rank + c2, false, false);

@@ -74,7 +74,7 @@ namespace sp {
 // Kernel families timed and flop-counted by the profiler.
 enum KernelId {
   KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_JACOBI, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
-  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_COUNT
+  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_COUNT
 };
 }  // namespace sp
 
@@ -88,6 +88,7 @@ struct sp_ctx {
   // profiler: CUDA events around every launch of a kernel family, and the
   // algorithmic flops the kernels count themselves (d_fc[kid])
   bool profiling = false;
+  int gemm_kid = sp::KID_GEMM;  // profiler bucket of k_gemm launches (call site)
   double* d_fc = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
   int64_t launches[sp::KID_COUNT] = {};
@@ -117,6 +118,13 @@ struct ProfScope {
   cudaEvent_t a = nullptr;
   ProfScope(sp_ctx* c, int k);
   ~ProfScope();
+};
+// Routes the k_gemm launches of a scope to a call-site bucket of the profiler.
+struct GemmSite {
+  sp_ctx* ctx;
+  int prev;
+  GemmSite(sp_ctx* c, int kid) : ctx(c), prev(c->gemm_kid) { ctx->gemm_kid = kid; }
+  ~GemmSite() { ctx->gemm_kid = prev; }
 };
 // Device flop counter of a family (null unless profiling).
 inline double* fc_ptr(sp_ctx* ctx, int kid) { return ctx->profiling ? ctx->d_fc + kid : nullptr; }

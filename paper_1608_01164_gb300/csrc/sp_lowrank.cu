@@ -26,8 +26,6 @@
 namespace sp {
 namespace {
 
-// shared memory available to the SVD kernel's working set (bytes)
-constexpr size_t kSvdSmemMax = 200 * 1024;
 
 __device__ __forceinline__ int dwidth(int w, const int* p) {
   if (!p) return w;
@@ -235,6 +233,7 @@ struct SvdJob {
   int Rmax;
   double* G;        // work (Rmax x Rmax)
   double* Vacc;     // work (Rmax x Rmax)
+  double* W3;       // work (Rmax x Rmax)
   double* SU;       // Rmax x cap: U~ Sigma (ru rows)
   double* SV;       // Rmax x cap: V~ (rv rows)
   int* pk;          // out: kept rank
@@ -252,65 +251,224 @@ __device__ __forceinline__ void rr_pair(int round, int p, int P, int& i, int& j)
   }
 }
 
-// One CTA (32 warps) per core.  When rows*cols + cols*cols doubles fit in
-// shared memory (SMEM = true) the working matrix G and the accumulated right
-// rotations V live there; otherwise in the global work buffers.  Each round of
-// the round-robin ordering has P/2 disjoint column pairs, processed by the
-// warps concurrently (one warp per pair: three dot products, then the
-// rotation of both columns of G and V).
-template <bool SMEM>
-__global__ void __launch_bounds__(1024) k_jacobi_svd(const SvdJob* __restrict__ jobs, double tol, int* flags,
-                                                     double* fc) {
-  const SvdJob jb = jobs[blockIdx.x];
-  const int ru = *jb.pru, rv = *jb.prv;
-  const bool tr = rv > ru;
-  const int rows = tr ? rv : ru, cols = tr ? ru : rv;
+// Block-wide argmax of v[c], c in [c0, c1) (v in shared memory); returns the
+// index (ties -> smallest) in *out_idx and the value in *out_val.
+__device__ void block_argmax(const double* v, int c0, int c1, double* red_v, int* red_i, int* out_idx,
+                             double* out_val) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double* sig = reinterpret_cast<double*>(smem_raw);
-  int* perm = reinterpret_cast<int*>(sig + jb.Rmax);
-  double* G;
-  double* V;
-  int ldg, ldv;
-  if (SMEM) {
-    G = sig + jb.Rmax + (jb.Rmax + 1) / 2;  // after sig (Rmax doubles) and perm (Rmax ints)
-    V = G + (size_t)rows * cols;
-    ldg = rows;
-    ldv = cols;
-  } else {
-    G = jb.G;
-    V = jb.Vacc;
-    ldg = jb.Rmax;
-    ldv = jb.Rmax;
+  double best = -1.0;
+  int bi = c1;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x)
+    if (v[c] > best) {
+      best = v[c];
+      bi = c;
+    }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ov > best || (ov == best && oi < bi)) {
+      best = ov;
+      bi = oi;
+    }
   }
-  __shared__ int s_rot;
-  __shared__ int s_k;
-  const int ldm = jb.Rmax;
-  for (int64_t e = threadIdx.x; e < (int64_t)rows * cols; e += blockDim.x) {
-    const int i = (int)(e % rows), c = (int)(e / rows);
-    G[i + (int64_t)c * ldg] = tr ? jb.M[c + (int64_t)i * ldm] : jb.M[i + (int64_t)c * ldm];
-  }
-  for (int64_t e = threadIdx.x; e < (int64_t)cols * cols; e += blockDim.x) {
-    const int i = (int)(e % cols), c = (int)(e / cols);
-    V[i + (int64_t)c * ldv] = (i == c) ? 1.0 : 0.0;
+  if (lane == 0) {
+    red_v[warp] = best;
+    red_i[warp] = bi;
   }
   __syncthreads();
-  const int P = cols + (cols & 1);
+  if (threadIdx.x == 0) {
+    double b = -1.0;
+    int ib = c1;
+    for (int w = 0; w < nw; ++w)
+      if (red_v[w] > b || (red_v[w] == b && red_i[w] < ib)) {
+        b = red_v[w];
+        ib = red_i[w];
+      }
+    *out_idx = ib;
+    *out_val = b;
+  }
+  __syncthreads();
+}
+
+// Householder reflector for column j of X (rows j..rows-1), stored in place
+// below the diagonal (v_0 = 1 implicit); returns tau (0: identity).  All
+// threads call it; the caller synchronises before using the column.
+__device__ double make_reflector(double* X, int64_t ld, int j, int rows, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_tau;
+  __shared__ double s_v0;
+  double part = 0.0;
+  for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) {
+    const double x = X[i + (int64_t)j * ld];
+    part = fma(x, x, part);
+  }
+  part = warp_sum(part);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sigma = 0.0;
+    for (int w = 0; w < nw; ++w) sigma += red[w];
+    const double x0 = X[j + (int64_t)j * ld];
+    if (sigma == 0.0) {
+      s_tau = 0.0;
+      s_v0 = 1.0;
+    } else {
+      const double mu = sqrt(x0 * x0 + sigma);
+      const double v0 = (x0 <= 0.0) ? x0 - mu : -sigma / (x0 + mu);
+      s_tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
+      s_v0 = v0;
+      X[j + (int64_t)j * ld] = mu;
+    }
+  }
+  __syncthreads();
+  const double tau = s_tau;
+  if (tau != 0.0) {
+    const double inv = 1.0 / s_v0;
+    for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) X[i + (int64_t)j * ld] *= inv;
+  }
+  __syncthreads();
+  return tau;
+}
+
+// Y(j:rows, c) -= tau v (v^T Y(j:rows, c)) for columns c in [c0, c1) of Y, v =
+// reflector j stored in V (column j, v_0 = 1); one warp per column.  With
+// nrm != null also stores ||Y(j+1:rows, c)||^2 in nrm[c] (pivoting norms).
+__device__ void apply_reflector(const double* V, int64_t ldv, int j, int rows, double tau, double* Y, int64_t ldy,
+                                int c0, int c1, double* nrm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = c0 + warp; c < c1; c += nw) {
+    double* y = Y + (int64_t)c * ldy;
+    const double* v = V + (int64_t)j * ldv;
+    if (tau != 0.0) {
+      double d = 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) d = fma(v[i], y[i], d);
+      const double yj = y[j];  // read before the synchronising reduction
+      d = warp_sum(d) + yj;
+      const double f = tau * d;
+      if (lane == 0) y[j] = yj - f;
+      for (int i = j + 1 + lane; i < rows; i += 32) y[i] -= f * v[i];
+    }
+    if (nrm) {
+      double q = 0.0;
+      for (int i = j + 1 + lane; i < rows; i += 32) q = fma(y[i], y[i], q);
+      q = warp_sum(q);
+      if (lane == 0) nrm[c] = q;
+    }
+  }
+}
+
+// Truncated SVD of the r_U x r_V core M = R_U R_V^T (one CTA per core):
+//  1. column-pivoted Householder QR  M P = Q1 [R11 R12; 0 R22], stopped when
+//     every remaining column norm is <= 1e-3 tol / sqrt(cols), so the dropped
+//     ||R22||_F <= 1e-3 tol;  r' = rows kept;
+//  2. Householder QR of the transpose of the r' x cols trapezoid T: T^T = Q2 R2;
+//  3. one-sided Jacobi on B = R2^T (r' x r'):  B J = U~ Sigma;
+//  4. M ~= (Q1 U~ Sigma)(P Q2 J)^T: keep sigma > tol, apply the reflectors.
+// Cost O(r' r_U r_V) instead of O(r_U^3) for a core of numerical rank r'.
+__global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jobs, double tol, int* flags,
+                                                   double* fc) {
+  const SvdJob jb = jobs[blockIdx.x];
+  const int ru = *jb.pru, rv = *jb.prv;
+  const int ld = jb.Rmax;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* M = const_cast<double*>(jb.M);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* nrm = reinterpret_cast<double*>(smem_raw);  // Rmax
+  double* tau1 = nrm + ld;                            // Rmax
+  double* tau2 = tau1 + ld;                           // Rmax
+  double* sig = tau2 + ld;                            // Rmax
+  int* perm = reinterpret_cast<int*>(sig + ld);       // Rmax
+  int* perm2 = perm + ld;                             // Rmax
+  __shared__ double red_v[32];
+  __shared__ int red_i[32];
+  __shared__ int s_p;
+  __shared__ double s_max;
+  __shared__ int s_rot;
+  __shared__ int s_k;
+  double nflop = 0.0;   // block-level stages, counted by thread 0
+  double nflopw = 0.0;  // per-warp Jacobi work, counted by each warp's lane 0
+  // ---- 1. column-pivoted QR of M
+  for (int c = warp; c < rv; c += nw) {
+    double q = 0.0;
+    for (int i = lane; i < ru; i += 32) q = fma(M[i + (int64_t)c * ld], M[i + (int64_t)c * ld], q);
+    q = warp_sum(q);
+    if (lane == 0) {
+      nrm[c] = q;
+      perm[c] = c;
+    }
+  }
+  __syncthreads();
+  const double thr = 1e-3 * tol / sqrt((double)(rv > 0 ? rv : 1));
+  const double thr2 = thr * thr;
+  int rp = 0;
+  const int rmin = ru < rv ? ru : rv;
+  for (int j = 0; j < rmin; ++j) {
+    // remaining norm of column c counts rows j..ru-1
+    block_argmax(nrm, j, rv, red_v, red_i, &s_p, &s_max);
+    if (s_max <= thr2) break;
+    const int p = s_p;
+    if (p != j) {
+      for (int i = threadIdx.x; i < ru; i += blockDim.x) {
+        const double t = M[i + (int64_t)j * ld];
+        M[i + (int64_t)j * ld] = M[i + (int64_t)p * ld];
+        M[i + (int64_t)p * ld] = t;
+      }
+      if (threadIdx.x == 0) {
+        const double t = nrm[j];
+        nrm[j] = nrm[p];
+        nrm[p] = t;
+        const int q = perm[j];
+        perm[j] = perm[p];
+        perm[p] = q;
+      }
+    }
+    __syncthreads();
+    const double tau = make_reflector(M, ld, j, ru, red_v);
+    if (threadIdx.x == 0) tau1[j] = tau;
+    apply_reflector(M, ld, j, ru, tau, M, ld, j + 1, rv, nrm);
+    nflop += 6.0 * (double)(ru - j) * (rv - j);
+    __syncthreads();
+    rp = j + 1;
+  }
+  // ---- 2. A2 = T^T (rv x rp), T = rows 0..rp-1 of the upper trapezoid
+  double* A2 = jb.G;
+  for (int64_t e = threadIdx.x; e < (int64_t)rv * rp; e += blockDim.x) {
+    const int c = (int)(e % rv), i = (int)(e / rv);
+    A2[c + (int64_t)i * ld] = (i <= c) ? M[i + (int64_t)c * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int j = 0; j < rp; ++j) {
+    const double tau = make_reflector(A2, ld, j, rv, red_v);
+    if (threadIdx.x == 0) tau2[j] = tau;
+    apply_reflector(A2, ld, j, rv, tau, A2, ld, j + 1, rp, nullptr);
+    nflop += 4.0 * (double)(rv - j) * (rp - j);
+    __syncthreads();
+  }
+  // ---- 3. Jacobi on B = R2^T (rp x rp), J accumulated
+  double* B = jb.Vacc;
+  double* J = jb.W3;
+  for (int64_t e = threadIdx.x; e < (int64_t)rp * rp; e += blockDim.x) {
+    const int i = (int)(e % rp), c = (int)(e / rp);
+    B[i + (int64_t)c * ld] = (c <= i) ? A2[c + (int64_t)i * ld] : 0.0;
+    J[i + (int64_t)c * ld] = (i == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  const int P = rp + (rp & 1);
   const double eps = 1e-15;
-  double nflop = 0.0;
-  for (int sweep = 0; sweep < 60 && cols > 1; ++sweep) {
+  for (int sweep = 0; sweep < 60 && rp > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
     __syncthreads();
     int rotated = 0;
     for (int round = 0; round < P - 1; ++round) {
-      for (int p = warp; p < P / 2; p += nw) {
-        int i, j;
-        rr_pair(round, p, P, i, j);
-        if (i >= cols || j >= cols) continue;
-        double* gi = G + (int64_t)i * ldg;
-        double* gj = G + (int64_t)j * ldg;
+      for (int pp = warp; pp < P / 2; pp += nw) {
+        int i, jj;
+        rr_pair(round, pp, P, i, jj);
+        if (i >= rp || jj >= rp) continue;
+        double* gi = B + (int64_t)i * ld;
+        double* gj = B + (int64_t)jj * ld;
         double a = 0.0, b = 0.0, g = 0.0;
-        for (int r = lane; r < rows; r += 32) {
+        for (int r = lane; r < rp; r += 32) {
           const double x = gi[r], y = gj[r];
           a = fma(x, x, a);
           b = fma(y, y, b);
@@ -319,23 +477,21 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(const SvdJob* __restrict__ 
         a = warp_sum(a);
         b = warp_sum(b);
         g = warp_sum(g);
-        nflop += 6.0 * rows;
+        nflopw += 6.0 * rp;
         if (g != 0.0 && fabs(g) > eps * sqrt(a * b)) {
-          nflop += 6.0 * rows + 6.0 * cols;
+          nflopw += 12.0 * rp;
           const double zeta = (b - a) / (2.0 * g);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double cs = rsqrt(1.0 + t * t), sn = cs * t;
-          for (int r = lane; r < rows; r += 32) {
+          double* ji = J + (int64_t)i * ld;
+          double* jj2 = J + (int64_t)jj * ld;
+          for (int r = lane; r < rp; r += 32) {
             const double x = gi[r], y = gj[r];
             gi[r] = cs * x - sn * y;
             gj[r] = sn * x + cs * y;
-          }
-          double* vi = V + (int64_t)i * ldv;
-          double* vj = V + (int64_t)j * ldv;
-          for (int r = lane; r < cols; r += 32) {
-            const double x = vi[r], y = vj[r];
-            vi[r] = cs * x - sn * y;
-            vj[r] = sn * x + cs * y;
+            const double u = ji[r], v = jj2[r];
+            ji[r] = cs * u - sn * v;
+            jj2[r] = sn * u + cs * v;
           }
           rotated = 1;
         }
@@ -347,27 +503,23 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(const SvdJob* __restrict__ 
     if (!s_rot) break;
     __syncthreads();
   }
-  if (fc && lane == 0 && nflop > 0.0) atomicAdd(fc, nflop);
-  // singular values = column norms
-  for (int c = warp; c < cols; c += nw) {
+  // ---- 4. singular values, order, truncation
+  for (int c = warp; c < rp; c += nw) {
     double a = 0.0;
-    for (int r = lane; r < rows; r += 32) {
-      const double x = G[r + (int64_t)c * ldg];
-      a = fma(x, x, a);
-    }
+    for (int r = lane; r < rp; r += 32) a = fma(B[r + (int64_t)c * ld], B[r + (int64_t)c * ld], a);
     a = warp_sum(a);
     if (lane == 0) sig[c] = sqrt(a);
   }
   __syncthreads();
-  for (int c = threadIdx.x; c < cols; c += blockDim.x) {
+  for (int c = threadIdx.x; c < rp; c += blockDim.x) {
     int pos = 0;
     const double sc = sig[c];
-    for (int d = 0; d < cols; ++d) pos += (sig[d] > sc) || (sig[d] == sc && d < c);
-    perm[pos] = c;
+    for (int d = 0; d < rp; ++d) pos += (sig[d] > sc) || (sig[d] == sc && d < c);
+    perm2[pos] = c;
   }
   if (threadIdx.x == 0) {
     int k = 0;
-    for (int c = 0; c < cols; ++c) k += sig[c] > tol;
+    for (int c = 0; c < rp; ++c) k += sig[c] > tol;
     if (k > jb.cap) {
       atomicOr(&flags[FLAG_RANK], 1);
       k = jb.cap;
@@ -377,23 +529,39 @@ __global__ void __launch_bounds__(1024) k_jacobi_svd(const SvdJob* __restrict__ 
   }
   __syncthreads();
   const int k = s_k;
-  const int ld = jb.Rmax;
+  // S_U = Q1 [B(:, perm2) ; 0]  (ru rows, k columns)
   for (int64_t e = threadIdx.x; e < (int64_t)ld * jb.cap; e += blockDim.x) {
     const int r = (int)(e % ld), p = (int)(e / ld);
-    double u = 0.0, v = 0.0;
-    if (p < k) {
-      const int c = perm[p];
-      const double s = sig[c];
-      if (!tr) {
-        if (r < ru) u = G[r + (int64_t)c * ldg];
-        if (r < rv) v = V[r + (int64_t)c * ldv];
-      } else {
-        if (r < ru) u = V[r + (int64_t)c * ldv] * s;
-        if (r < rv) v = (s > 0.0) ? G[r + (int64_t)c * ldg] / s : 0.0;
-      }
-    }
-    jb.SU[r + (int64_t)p * ld] = u;
-    jb.SV[r + (int64_t)p * ld] = v;
+    jb.SU[r + (int64_t)p * ld] = (p < k && r < rp) ? B[r + (int64_t)perm2[p] * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int j = rp - 1; j >= 0; --j) {
+    apply_reflector(M, ld, j, ru, tau1[j], jb.SU, ld, 0, k, nullptr);
+    __syncthreads();
+  }
+  // W = Q2 [J(:, perm2); 0] (rv rows) in B's buffer, then S_V = P W
+  double* W = jb.Vacc;
+  for (int64_t e = threadIdx.x; e < (int64_t)ld * k; e += blockDim.x) {
+    const int r = (int)(e % ld), p = (int)(e / ld);
+    W[r + (int64_t)p * ld] = (r < rp) ? J[r + (int64_t)perm2[p] * ld] : 0.0;
+  }
+  __syncthreads();
+  for (int j = rp - 1; j >= 0; --j) {
+    apply_reflector(A2, ld, j, rv, tau2[j], W, ld, 0, k, nullptr);
+    __syncthreads();
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)ld * jb.cap; e += blockDim.x) {
+    const int r = (int)(e % ld), p = (int)(e / ld);
+    if (p >= k || r >= rv) jb.SV[r + (int64_t)p * ld] = 0.0;
+  }
+  for (int64_t e = threadIdx.x; e < (int64_t)rv * k; e += blockDim.x) {
+    const int r = (int)(e % rv), p = (int)(e / rv);
+    jb.SV[perm[r] + (int64_t)p * ld] = W[r + (int64_t)p * ld];
+  }
+  if (fc) {
+    if (threadIdx.x == 0) nflop += 4.0 * rp * ((double)ru + rv) * k;  // the two reflector applications
+    const double f = (threadIdx.x == 0 ? nflop : 0.0) + (lane == 0 ? nflopw : 0.0);
+    if (f > 0.0) atomicAdd(fc, f);
   }
 }
 
@@ -567,9 +735,9 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     plan_side(g.WV, b.q, b.q, g.R, Rm, RV, SV, b.rank_out, b.cap, b.Vout, b.ldv_out, qrl, apl, keep, st);
     // M = R_U R_V^T (ru x rv, inner dimension R)
     core.push_back(gt(RU, Rm, RV, Rm, M, Rm, Rm, Rm, Rm, 1.0, 0.0, g.ru, g.rv, g.R));
-    keep.emplace_back((size_t)Rm * Rm * 2 * sizeof(double) + 16, st);
+    keep.emplace_back((size_t)Rm * Rm * 3 * sizeof(double) + 16, st);
     double* Gw = keep.back().as<double>();
-    svd[t] = SvdJob{M, g.ru, g.rv, Rm, Gw, Gw + (size_t)Rm * Rm, SU, SV, b.rank_out, b.cap};
+    svd[t] = SvdJob{M, g.ru, g.rv, Rm, Gw, Gw + (size_t)Rm * Rm, Gw + 2 * (size_t)Rm * Rm, SU, SV, b.rank_out, b.cap};
   }
   // 1. gather
   {
@@ -593,44 +761,17 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
   }
   // 3. cores
   gemm_batched(ctx, false, true, core);
-  // 4. SVD + truncation: cores whose working set fits in shared memory take
-  // the shared-memory kernel, the rest the global-memory one
+  // 4. truncated SVD of every core (rank-revealing QR, then Jacobi on the
+  // kept triangle)
   {
-    std::vector<SvdJob> small, large;
-    int maxR_small = 1, maxR_large = 1;
-    size_t need_small = 0;
-    for (int t = 0; t < nb; ++t) {
-      const size_t R = (size_t)Rmax[t];
-      const size_t bytes = R * (sizeof(double) + sizeof(int)) + 2 * R * R * sizeof(double) + 64;
-      if (bytes <= kSvdSmemMax) {
-        small.push_back(svd[t]);
-        maxR_small = std::max(maxR_small, Rmax[t]);
-        need_small = std::max(need_small, bytes);
-      } else {
-        large.push_back(svd[t]);
-        maxR_large = std::max(maxR_large, Rmax[t]);
-      }
-    }
-    ProfScope ps(ctx, KID_JACOBI);
-    if (!small.empty()) {
-      DBuf d = upload(small, st);
-      check_cuda(cudaFuncSetAttribute(k_jacobi_svd<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)kSvdSmemMax),
+    DBuf d = upload(svd, st);
+    const size_t sm = (size_t)maxR * (4 * sizeof(double) + 2 * sizeof(int)) + 64;
+    if (sm > 48 * 1024)
+      check_cuda(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "smem attr");
-      k_jacobi_svd<true><<<(unsigned)small.size(), 1024, need_small, st>>>(d.as<SvdJob>(), tol, ctx->d_flags,
-                                                                            fc_ptr(ctx, KID_JACOBI));
-      check_launch("k_jacobi_svd");
-    }
-    if (!large.empty()) {
-      DBuf d = upload(large, st);
-      const size_t sm = (size_t)maxR_large * (sizeof(double) + sizeof(int)) + 64;
-      if (sm > 48 * 1024)
-        check_cuda(cudaFuncSetAttribute(k_jacobi_svd<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                   "smem attr");
-      k_jacobi_svd<false><<<(unsigned)large.size(), 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags,
-                                                                     fc_ptr(ctx, KID_JACOBI));
-      check_launch("k_jacobi_svd");
-    }
+    ProfScope ps(ctx, KID_JACOBI);
+    k_core_svd<<<(unsigned)nb, 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags, fc_ptr(ctx, KID_JACOBI));
+    check_launch("k_core_svd");
   }
   // 5. apply reflectors top-down
   for (auto& lvl : apl) {
