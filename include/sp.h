@@ -179,6 +179,26 @@ int sp_inertia(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t lda
  * lam_nu_hi > lambda_nu and lam_nu1_lo <= lambda_{nu+1}.  Synchronising. */
 int sp_locate_shift(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int64_t nu, double* mu,
                     double* lam_nu_hi, double* lam_nu1_lo);
+/* Inertia counts without any device allocation, for callers that cannot call
+ * cudaMalloc: for example a host program that hands the whole GPU to its own
+ * memory pool up front, or code that must not touch the CUDA allocator while
+ * it runs.  The paper has no counterpart; it computes the same counts as
+ * sp_inertia.
+ *   ab (band, ldab >= b+1), shifts (nshift doubles) and counts (nshift
+ *   int64) are DEVICE pointers owned by the caller.
+ *   Scratch: a library-owned device array of SP_NOALLOC_SCRATCH_DOUBLES
+ *   doubles (8 MiB), held by every GPU that loads the library until the
+ *   process exits.  A call needs 520 + nshift * (b*b + b) doubles of it (b > 1;
+ *   520 for b <= 1); larger requests return SP_EINVAL with a message.
+ *   The first call on a device looks the array's device address up (with that
+ *   device current) and caches it; make that first call before any CUDA stream
+ *   capture.  Every call reuses the same array: calls whose work overlaps on the
+ *   GPU (other streams, other threads) race on it and must be serialised by the
+ *   caller.  Enqueues on the context stream; does not synchronise. */
+#define SP_NOALLOC_SCRATCH_DOUBLES (1 << 20)
+int sp_inertia_noalloc(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int32_t nshift,
+                       const double* shifts, int64_t* counts);
+
 /* QDWH start: alpha >= ||A - mu I||_2 and l0 <= sigma_min((A - mu I)/alpha)
  * from inertia brackets of the extreme eigenvalues and of the eigenvalues
  * next to mu.  Synchronising. */

@@ -25,6 +25,7 @@ NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
 
 SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_EBREAKDOWN, SP_ENONFINITE, SP_ERANK, SP_ETIMEOUT, SP_EINTERNAL = range(9)
 SP_FP64, SP_MIXED_FP32 = 0, 1
+SP_NOALLOC_SCRATCH_DOUBLES = 1 << 20
 
 # every entry point declared in include/sp.h
 EXPORTS = [
@@ -33,7 +34,7 @@ EXPORTS = [
     "sp_hodlr_info", "sp_hodlr_destroy", "sp_hodlr_add", "sp_hodlr_mult", "sp_hodlr_cholesky",
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_kernel_name", "sp_kernel_count",
-    "sp_launch_count",
+    "sp_launch_count", "sp_inertia_noalloc",
 ]
 
 
@@ -120,6 +121,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_kernel_name": (ctypes.c_char_p, [I]),
         "sp_kernel_count": (I, []),
         "sp_launch_count": (I64, []),
+        "sp_inertia_noalloc": (I, [P, I64, I32, P, I64, I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -313,3 +315,8 @@ def sp_ctx_profile(ctx):
 
 def sp_launch_count() -> int:
     return int(_lib.sp_launch_count())
+
+
+def sp_inertia_noalloc(ctx, n: int, b: int, ab, ldab: int, nshift: int, shifts, counts):
+    """Device band, shifts and counts; scratch inside the library (no allocation)."""
+    _check(ctx, _lib.sp_inertia_noalloc(ctx, n, b, _ptr(ab), ldab, nshift, _ptr(shifts), _ptr(counts)))

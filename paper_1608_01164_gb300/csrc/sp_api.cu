@@ -28,6 +28,8 @@ void locate_shift(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t l
 void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
                 double* l0);
 void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma);
+void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
+                            const double* shifts_dev, int64_t* counts_dev);
 int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
 
 namespace {
@@ -488,6 +490,14 @@ int sp_inertia(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t lda
     check_cuda(cudaMemcpyAsync(counts, c.p, nshift * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx->stream), "counts");
     check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
   });
+}
+
+// Inertia counts for callers that cannot allocate device memory: scratch in
+// a file-scope device array (see include/sp.h); no cudaMalloc/cudaFree.
+int sp_inertia_noalloc(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int32_t nshift,
+                       const double* shifts, int64_t* counts) {
+  if (!ctx || !ab || !shifts || !counts || n < 1 || b < 0 || ldab < b + 1 || nshift < 0) return SP_EINVAL;
+  return guarded(ctx, [&] { inertia_counts_noalloc(ctx, n, b, ab, ldab, nshift, shifts, counts); });
 }
 
 int sp_locate_shift(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int64_t nu, double* mu,

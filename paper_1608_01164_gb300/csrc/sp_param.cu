@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
+#include <mutex>
+#include <string>
 #include <vector>
 
 #include "sp_internal.h"
@@ -94,7 +96,98 @@ __global__ void k_absmax(const double* __restrict__ ab, int64_t ldab, int64_t n,
   if ((threadIdx.x & 31) == 0) out[blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32] = m;
 }
 
+// ---- no-allocation variant: scratch in a file-scope device array ----------
+// Layout: [0, 512) absmax partials of k_absmax, [512] pivmin, [520, ...)
+// per-shift LDL^T rings.
+__device__ __align__(256) double g_noalloc_scratch[SP_NOALLOC_SCRATCH_DOUBLES];
+
+__global__ void k_pivmin_from_partials(double* scratch, int nparts) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double amax = 1.0;
+    for (int i = 0; i < nparts; ++i) amax = fmax(amax, scratch[i]);
+    scratch[512] = DBL_MIN * amax * amax;
+  }
+}
+
+__global__ void k_inertia_noalloc(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+                                  const double* __restrict__ shifts, int nshift, int64_t* __restrict__ counts,
+                                  const double* __restrict__ scratch) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nshift) return;
+  const double pivmin = scratch[512];
+  const double sigma = shifts[t];
+  int64_t cnt = 0;
+  if (b == 1) {
+    double d = 1.0;
+    for (int64_t i = 0; i < n; ++i) {
+      const double e = (i == 0) ? 0.0 : ab[1 + (i - 1) * ldab];
+      d = (ab[i * ldab] - sigma) - ((i == 0) ? 0.0 : e * e / d);
+      if (fabs(d) < pivmin) d = -pivmin;
+      cnt += d < 0.0;
+    }
+  } else if (b == 0) {
+    for (int64_t i = 0; i < n; ++i) cnt += ab[i * ldab] < sigma;
+  } else {
+    double* Lr = const_cast<double*>(scratch) + 520 + (size_t)t * (b * b + b);
+    double* Dr = Lr + b * b;
+    for (int64_t j = 0; j < n; ++j) {
+      double dj = ab[j * ldab] - sigma;
+      const int64_t k0 = j - b > 0 ? j - b : 0;
+      for (int64_t k = k0; k < j; ++k) {
+        const double l = Lr[(k % b) * b + (j - k - 1)];
+        dj -= l * l * Dr[k % b];
+      }
+      if (fabs(dj) < pivmin) dj = -pivmin;
+      cnt += dj < 0.0;
+      const double inv = 1.0 / dj;
+      double* Lj = Lr + (j % b) * b;
+      for (int64_t i = j + 1; i <= j + b; ++i) {
+        double s = (i < n) ? ab[(i - j) + j * ldab] : 0.0;
+        const int64_t kk0 = i - b > 0 ? i - b : 0;
+        for (int64_t k = kk0; k < j; ++k) s -= Lr[(k % b) * b + (i - k - 1)] * Lr[(k % b) * b + (j - k - 1)] * Dr[k % b];
+        Lj[i - j - 1] = s * inv;
+      }
+      Dr[j % b] = dj;
+    }
+  }
+  counts[t] = cnt;
+}
+
 }  // namespace
+
+// Device address of the no-allocation scratch on the current device, looked
+// up once per device (the host-side symbol is only a stand-in).
+double* noalloc_scratch_ptr() {
+  static std::mutex mu;
+  static double* ptrs[64] = {};
+  int dev = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev < 0 || dev >= 64) fail(SP_EINVAL, "device ordinal out of range for the no-allocation scratch");
+  std::lock_guard<std::mutex> lk(mu);
+  if (!ptrs[dev]) {
+    void* p = nullptr;
+    check_cuda(cudaGetSymbolAddress(&p, g_noalloc_scratch), "cudaGetSymbolAddress(no-allocation scratch)");
+    ptrs[dev] = static_cast<double*>(p);
+  }
+  return ptrs[dev];
+}
+
+void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
+                            const double* shifts_dev, int64_t* counts_dev) {
+  const size_t need = 520 + (b > 1 ? (size_t)nshift * ((size_t)b * b + b) : 0);
+  if (need > (size_t)SP_NOALLOC_SCRATCH_DOUBLES)
+    fail(SP_EINVAL, "sp_inertia_noalloc: nshift * (b*b + b) + 520 = " + std::to_string(need) +
+                        " doubles exceeds the scratch of " + std::to_string(SP_NOALLOC_SCRATCH_DOUBLES));
+  if (nshift <= 0) return;
+  double* scratch = noalloc_scratch_ptr();
+  k_absmax<<<64, 256, 0, ctx->stream>>>(ab_dev, ldab, n, b, scratch);
+  check_launch("k_absmax");
+  k_pivmin_from_partials<<<1, 32, 0, ctx->stream>>>(scratch, 64 * (256 / 32));
+  check_launch("k_pivmin_from_partials");
+  k_inertia_noalloc<<<(nshift + 63) / 64, 64, 0, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev,
+                                                                scratch);
+  check_launch("k_inertia_noalloc");
+}
 
 // counts_dev[i] = #{lambda < shifts_dev[i]} (device arrays)
 void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
