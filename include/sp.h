@@ -49,9 +49,10 @@ extern "C" {
 
 /* Precision modes for sp_qdwh_sign. */
 #define SP_FP64 0        /* every step in binary64 */
-#define SP_MIXED_FP32 1  /* well-conditioned Cholesky steps in residual form with
-                            binary32 leaf/factor GEMMs, binary64 recompression,
-                            then binary64 Newton-Schulz polish */
+#define SP_MIXED_FP32 1  /* Cholesky steps with 1 - l_k^2 <= 1e-2 in residual form
+                            X + (a-1) X Z^{-1} (I - X^2) with binary32 GEMM
+                            arithmetic (binary64 storage, residual, sum and
+                            recompression), then binary64 Newton-Schulz polish */
 
 typedef struct sp_ctx* sp_ctx_t;
 typedef struct sp_hodlr* sp_hodlr_t;
@@ -81,6 +82,7 @@ typedef struct {
    * inverse factor), the two products with the inverse factor, and the final
    * combination + symmetrisation (CUDA events, summed over iterations) */
   double ms_mult, ms_factor, ms_solve, ms_combine;
+  double ms_polish;        /* binary64 Newton-Schulz polish (mixed precision) */
 } sp_info;
 
 /* Returns opts filled with the defaults listed above. */
@@ -123,7 +125,7 @@ int64_t sp_launch_count(void);
  *   blocks); tol > 0 is the absolute truncation tolerance (Sec. 3.1.1,
  *   "absolute truncation tolerance epsilon") kept with the matrix and used by
  *   every later formatted operation on it; rank_cap >= 2b is the per-block
- *   rank capacity (0 selects 160).
+ *   rank capacity (0 selects max(160, 20b)).
  *   ab: host or device pointer.  On success *out is a new handle. */
 int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
                        int32_t leaf, double tol, int32_t rank_cap, sp_hodlr_t* out);
@@ -133,6 +135,21 @@ int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int
  * needs).  opts may be NULL (defaults).  On success *sign_out is a new
  * handle; info (may be NULL) receives diagnostics. */
 int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts, sp_hodlr_t* sign_out, sp_info* info);
+
+/* Projectors of many independent banded instances (uneven n, b and mu):
+ * instance i is A_i = ab[i] (lower band storage, ldab[i] >= b[i]+1, host or
+ * device pointer) shifted by mu[i]; P_out[i] receives Pi_{<mu_i}(A_i) in HODLR
+ * format (Algorithm 3 per instance).  Instances are spread over `nstreams`
+ * CUDA streams (0 selects 16), each driven by its own host worker thread, so
+ * the small kernels of many instances run concurrently; larger instances are
+ * started first.  leaf = 0 picks the leaf size per instance from n and b
+ * (64 for n <= 2048, 128 for n <= 8192, else 256, at least 2b).  infos (may be
+ * NULL) receives per-instance diagnostics.  On return all work has finished
+ * and the handles belong to the context's stream.  On failure no handle is
+ * returned and the status of the first failing instance is reported. */
+int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const int32_t* b, const double* const* ab,
+                         const int64_t* ldab, const double* mu, int32_t leaf, double tol, int32_t rank_cap,
+                         const sp_qdwh_opts* opts, int32_t nstreams, sp_hodlr_t* P_out, sp_info* infos);
 
 /* P = (I - S) / 2 (Algorithm 3, last line); new handle in *P_out. */
 int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out);
@@ -152,6 +169,9 @@ int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr);
 /* Sizes of a handle: order, tree depth, largest off-diagonal rank and device
  * bytes held.  Synchronising. */
 int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32_t* max_rank, size_t* bytes);
+/* Releases a handle's device memory stream-ordered on the stream of the
+ * context that created it (work already enqueued there completes first); call
+ * it before that stream is destroyed. */
 void sp_hodlr_destroy(sp_hodlr_t M);
 
 /* ---- formatted HODLR arithmetic (Table "complexity_HODLR") ---- */

@@ -34,7 +34,7 @@ EXPORTS = [
     "sp_hodlr_info", "sp_hodlr_destroy", "sp_hodlr_add", "sp_hodlr_mult", "sp_hodlr_cholesky",
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_kernel_name", "sp_kernel_count",
-    "sp_launch_count", "sp_inertia_noalloc",
+    "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector",
 ]
 
 
@@ -57,7 +57,7 @@ class sp_info(ctypes.Structure):
                 ("bytes", ctypes.c_size_t), ("ms_param", ctypes.c_double), ("ms_qr", ctypes.c_double),
                 ("ms_chol", ctypes.c_double), ("ms_total", ctypes.c_double), ("flops", ctypes.c_double),
                 ("ms_mult", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
-                ("ms_combine", ctypes.c_double)]
+                ("ms_combine", ctypes.c_double), ("ms_polish", ctypes.c_double)]
 
 
 def build(force: bool = False, jobs: int = 6) -> str:
@@ -122,6 +122,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_kernel_count": (I, []),
         "sp_launch_count": (I64, []),
         "sp_inertia_noalloc": (I, [P, I64, I32, P, I64, I32, P, P]),
+        "sp_batched_projector": (I, [P, I32, P, P, P, P, P, I32, D, I32, ctypes.POINTER(sp_qdwh_opts), I32, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -320,3 +321,23 @@ def sp_launch_count() -> int:
 def sp_inertia_noalloc(ctx, n: int, b: int, ab, ldab: int, nshift: int, shifts, counts):
     """Device band, shifts and counts; scratch inside the library (no allocation)."""
     _check(ctx, _lib.sp_inertia_noalloc(ctx, n, b, _ptr(ab), ldab, nshift, _ptr(shifts), _ptr(counts)))
+
+
+def sp_batched_projector(ctx, bands, mus, leaf: int = 0, tol: float = 1e-10, rank_cap: int = 0, opts=None,
+                         nstreams: int = 0):
+    """bands: list of (n, b+1) band arrays (numpy: host, torch: device); returns
+    (list of projector handles, list of sp_info)."""
+    import numpy as _np
+    nb = len(bands)
+    n = _np.array([x.shape[0] for x in bands], dtype=_np.int64)
+    b = _np.array([x.shape[1] - 1 for x in bands], dtype=_np.int32)
+    ld = _np.array([x.shape[1] for x in bands], dtype=_np.int64)
+    ptrs = (ctypes.c_void_p * max(nb, 1))(*[_ptr(x) for x in bands])
+    mu = _np.ascontiguousarray(mus, dtype=_np.float64)
+    out = (ctypes.c_void_p * max(nb, 1))()
+    infos = (sp_info * max(nb, 1))()
+    _check(ctx, _lib.sp_batched_projector(ctx, nb, n.ctypes.data, b.ctypes.data, ctypes.cast(ptrs, ctypes.c_void_p),
+                                          ld.ctypes.data, mu.ctypes.data, leaf, float(tol), rank_cap,
+                                          ctypes.byref(opts) if opts is not None else None, nstreams,
+                                          ctypes.cast(out, ctypes.c_void_p), ctypes.cast(infos, ctypes.c_void_p)))
+    return [ctypes.c_void_p(out[i]) for i in range(nb)], [infos[i] for i in range(nb)]

@@ -17,7 +17,11 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <atomic>
+#include <mutex>
 #include <new>
+#include <numeric>
+#include <thread>
 
 #include "sp_internal.h"
 
@@ -33,6 +37,9 @@ void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev,
 int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
 
 namespace {
+
+// iterations with 1 - l_k^2 <= this take the mixed-precision residual step
+constexpr double kMixedThreshold = 1e-2;
 
 template <class F>
 int guarded(sp_ctx* ctx, F&& f) {
@@ -162,6 +169,60 @@ sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c
   return Xn.release();
 }
 
+// Mixed-precision Cholesky-based step in residual form (for iterations whose
+// lower bound l_k has 1 - l_k^2 small):  f(x) - x = (a-1) x (1-x^2)/(1+c x^2)
+// (b - c = 1 - a), so
+//   X+ = X + (a - 1) X Z^{-1} R,   R = I - X^2,  Z = I + c X^2,
+// with R and the final sum in binary64 and the factorisation, the two
+// products with the inverse factor and X * (Z^{-1} R) using binary32 GEMM
+// arithmetic (recompression stays binary64).  The binary32 error multiplies
+// ||R|| ~ 1 - l_k^2 instead of ||X|| ~ 1.
+sp_hodlr* mixed_step(sp_ctx* ctx, const sp_hodlr* X, double a, double c, sp_info* inf) {
+  Timer t1(ctx->stream);
+  Owned Z(hodlr_mult(ctx, X, X));
+  Owned R(hodlr_add(ctx, -1.0, Z.p, 0.0, nullptr, 1.0));
+  hodlr_scale_shift(ctx, Z.p, c, 1.0);
+  inf->ms_mult += t1.stop();
+  Owned D(nullptr);
+  {
+    Fp32Gemms fp32(ctx);
+    Timer t2(ctx->stream);
+    sp_hodlr *lf = nullptr, *li = nullptr;
+    hodlr_cholesky_inv(ctx, Z.p, &lf, &li);
+    Owned Lf(lf), Li(li);
+    Z.reset(nullptr);
+    Lf.reset(nullptr);
+    inf->ms_factor += t2.stop();
+    Timer t3(ctx->stream);
+    Owned Y(hodlr_mult(ctx, Li.p, R.p));
+    Owned LiT(hodlr_transpose(ctx, Li.p));
+    Li.reset(nullptr);
+    Owned W(hodlr_mult(ctx, LiT.p, Y.p));
+    Y.reset(nullptr);
+    D.reset(hodlr_mult(ctx, X, W.p));
+    inf->ms_solve += t3.stop();
+  }
+  Timer t4(ctx->stream);
+  Owned Xn(hodlr_add(ctx, 1.0, X, a - 1.0, D.p, 0.0));
+  D.reset(nullptr);
+  hodlr_symmetrize(ctx, Xn.p);
+  inf->ms_combine += t4.stop();
+  return Xn.release();
+}
+
+// Binary64 Newton-Schulz step for the sign function in residual form:
+// X <- X + X (I - X^2) / 2  (= X (3I - X^2)/2).
+sp_hodlr* newton_schulz_step(sp_ctx* ctx, const sp_hodlr* X) {
+  Owned XX(hodlr_mult(ctx, X, X));
+  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0));
+  XX.reset(nullptr);
+  Owned D(hodlr_mult(ctx, X, R.p));
+  R.reset(nullptr);
+  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0));
+  hodlr_symmetrize(ctx, Xn.p);
+  return Xn.release();
+}
+
 // QR-based first step on the band kept by A (A = A - mu I in HODLR)
 sp_hodlr* qr_step(sp_ctx* ctx, const sp_hodlr* A, double alpha, double a, double b, double c) {
   const double sc = std::sqrt(c);
@@ -280,7 +341,7 @@ const char* sp_kernel_name(int kernel) {
   static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_jacobi_svd", "k_gather",
                                          "k_leaf_potrf", "k_leaf_trsm", "k_givens", "k_replay_leaf",
                                          "k_replay_track", "k_inertia", "misc", "k_gemm[apply]",
-                                         "k_gemm[chol]", "k_gemm[mult]"};
+                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm[fp32]"};
   return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
 }
 
@@ -291,7 +352,7 @@ int64_t sp_launch_count(void) { return launch_count(); }
 int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, int32_t leaf,
                        double tol, int32_t rank_cap, sp_hodlr_t* out) {
   if (!ctx || !out || !ab) return SP_EINVAL;
-  if (rank_cap == 0) rank_cap = 160;
+  if (rank_cap == 0) rank_cap = std::max(160, 20 * b);
   if (n < 1 || b < 1 || ldab < b + 1 || leaf < 2 || leaf < 2 * b || !(tol > 0.0) || rank_cap < 2 * b) {
     ctx->err = "sp_hodlr_from_band: need n >= 1, b >= 1, ldab >= b+1, leaf >= max(2, 2b), tol > 0, rank_cap >= 2b";
     return SP_EINVAL;
@@ -307,8 +368,10 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
   sp_qdwh_opts o;
   sp_qdwh_opts_default(&o);
   if (opts_in) o = *opts_in;
-  if (o.max_iter < 1 || o.max_iter > 16 || !(o.delta > 0.0) || o.qr_steps < 0 || o.qr_steps > 1) {
-    ctx->err = "sp_qdwh_sign: invalid options (max_iter in 1..16, delta > 0, qr_steps in {0, 1})";
+  if (o.max_iter < 1 || o.max_iter > 16 || !(o.delta > 0.0) || o.qr_steps < 0 || o.qr_steps > 1 ||
+      (o.precision != SP_FP64 && o.precision != SP_MIXED_FP32) || o.polish_steps < 0 || o.polish_steps > 4) {
+    ctx->err = "sp_qdwh_sign: invalid options (max_iter in 1..16, delta > 0, qr_steps in {0, 1}, precision, "
+               "polish_steps in 0..4)";
     return SP_EINVAL;
   }
   if (o.qr_steps == 1 && !A->band) {
@@ -368,11 +431,23 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
         if (!X.p) {
           X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
         }
-        X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k], &inf));
-        inf.kind[k] = 2;
+        const bool mixed = o.precision == SP_MIXED_FP32 && (1.0 - ls[k] * ls[k]) <= kMixedThreshold;
+        if (mixed) {
+          X.reset(mixed_step(ctx, X.p, as[k], cs[k], &inf));
+          inf.kind[k] = 3;
+        } else {
+          X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k], &inf));
+          inf.kind[k] = 2;
+        }
         check_flags(ctx, "Cholesky-based step");
         inf.ms_chol += t.stop();
       }
+    }
+    if (o.precision == SP_MIXED_FP32 && X.p) {
+      Timer t(ctx->stream);
+      for (int p = 0; p < o.polish_steps; ++p) X.reset(newton_schulz_step(ctx, X.p));
+      check_flags(ctx, "Newton-Schulz polish");
+      inf.ms_polish = t.stop();
     }
     if (!X.p) X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
     inf.iters = K;
@@ -385,6 +460,95 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
     }
     *sign_out = X.release();
   });
+}
+
+static int auto_leaf(int64_t n, int b) {
+  int leaf = n <= 2048 ? 64 : (n <= 8192 ? 128 : 256);
+  return std::max(leaf, std::max(2 * b, 2));
+}
+
+int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const int32_t* b, const double* const* ab,
+                         const int64_t* ldab, const double* mu, int32_t leaf, double tol, int32_t rank_cap,
+                         const sp_qdwh_opts* opts, int32_t nstreams, sp_hodlr_t* P_out, sp_info* infos) {
+  if (!ctx || nbatch < 0 || (nbatch > 0 && (!n || !b || !ab || !ldab || !mu || !P_out))) return SP_EINVAL;
+  for (int i = 0; i < nbatch; ++i)
+    if (n[i] < 1 || b[i] < 1 || !ab[i] || ldab[i] < b[i] + 1 || (leaf > 0 && leaf < 2 * b[i])) {
+      ctx->err = "sp_batched_projector: invalid instance " + std::to_string(i);
+      return SP_EINVAL;
+    }
+  if (nbatch == 0) return SP_OK;
+  const int T = std::max(1, std::min(nstreams > 0 ? nstreams : 16, std::min(nbatch, 64)));
+  std::vector<int> order(nbatch);
+  std::iota(order.begin(), order.end(), 0);
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return n[x] * (int64_t)b[x] > n[y] * (int64_t)b[y]; });
+  std::vector<sp_hodlr_t> outs(nbatch, nullptr);
+  std::atomic<int> next{0};
+  std::atomic<int> first_err{SP_OK};
+  std::mutex mu_err;
+  std::string err_msg;
+  auto worker = [&]() {
+    sp_ctx sub;
+    sub.device = ctx->device;
+    sub.num_sms = ctx->num_sms;
+    cudaSetDevice(ctx->device);
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaMalloc(&sub.d_flags, sizeof(int) * NFLAGS) != cudaSuccess ||
+        cudaMemset(sub.d_flags, 0, sizeof(int) * NFLAGS) != cudaSuccess) {
+      int expect = SP_OK;
+      first_err.compare_exchange_strong(expect, SP_ECUDA);
+      if (s) cudaStreamDestroy(s);
+      return;
+    }
+    sub.stream = s;
+    std::vector<int> mine;
+    for (;;) {
+      if (first_err.load() != SP_OK) break;
+      const int k = next.fetch_add(1);
+      if (k >= nbatch) break;
+      const int i = order[k];
+      sp_hodlr_t A = nullptr, S = nullptr, P = nullptr;
+      sp_info inf;
+      int rc = sp_hodlr_from_band(&sub, n[i], b[i], ab[i], ldab[i], mu[i], leaf > 0 ? leaf : auto_leaf(n[i], b[i]),
+                                  tol, rank_cap, &A);
+      if (rc == SP_OK) rc = sp_qdwh_sign(&sub, A, opts, &S, infos ? &inf : nullptr);
+      if (rc == SP_OK) rc = sp_projector(&sub, S, &P);
+      hodlr_free(A);
+      hodlr_free(S);
+      if (rc != SP_OK) {
+        int expect = SP_OK;
+        if (first_err.compare_exchange_strong(expect, rc)) {
+          std::lock_guard<std::mutex> lk(mu_err);
+          err_msg = "instance " + std::to_string(i) + ": " + sub.err;
+        }
+        hodlr_free(P);
+        break;
+      }
+      outs[i] = P;
+      if (infos) infos[i] = inf;
+      mine.push_back(i);
+    }
+    cudaStreamSynchronize(s);
+    // the results now belong to the caller's stream
+    for (int i : mine) {
+      outs[i]->stream = ctx->stream;
+      outs[i]->tree->stream = ctx->stream;
+    }
+    cudaFree(sub.d_flags);
+    sub.d_flags = nullptr;
+    cudaStreamDestroy(s);
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < T; ++t) th.emplace_back(worker);
+  for (auto& x : th) x.join();
+  const int rc = first_err.load();
+  if (rc != SP_OK) {
+    for (auto* P : outs) hodlr_free(P);
+    ctx->err = err_msg;
+    return rc;
+  }
+  for (int i = 0; i < nbatch; ++i) P_out[i] = outs[i];
+  return SP_OK;
 }
 
 int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out) {

@@ -84,7 +84,72 @@ __device__ __forceinline__ int dsize(int s, const int* p) {
   return s;
 }
 
-template <bool TA, bool TB>
+// MT = double: binary64 throughout.  MT = float: operands rounded to
+// binary32 when staged, binary32 FMA accumulation, result widened to binary64
+// (the mixed-precision steps; storage stays binary64).
+//
+// The grid is laid out in 64 x 64 output tiles; each CTA then computes only
+// the part of its tile inside the actual (device-resident) m x n: a
+// (16 MI) x (16 MJ) sub-tile with MI, MJ in {1, 2, 4}, each of the 256
+// threads an MI x MJ micro-tile.  Rank-sized dimensions (~30 of a capacity of
+// 160) thus cost no padded FMAs.
+template <bool TA, bool TB, typename MT, int MI, int MJ>
+__device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int row0, int col0, int kbeg, int kend,
+                                          int atomic, MT (*As)[kGT + 1], MT (*Bs)[kGT + 1]) {
+  constexpr int TM = 16 * MI, TN = 16 * MJ;
+  const int tid = threadIdx.x, r = tid & 15, c = tid >> 4;
+  MT acc[MI][MJ];
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) acc[i][j] = (MT)0;
+  for (int kb = kbeg; kb < kend; kb += kGK) {
+    for (int e = tid; e < TM * kGK; e += 256) {
+      int row, kk;
+      if (!TA) { row = e % TM; kk = e / TM; } else { kk = e % kGK; row = e / kGK; }
+      const int gr = row0 + row, gk = kb + kk;
+      double v = 0.0;
+      if (gr < m && gk < kend) v = TA ? t.A[gk + (int64_t)gr * t.lda] : t.A[gr + (int64_t)gk * t.lda];
+      As[kk][row] = (MT)v;
+    }
+    for (int e = tid; e < TN * kGK; e += 256) {
+      int col, kk;
+      if (!TB) { kk = e % kGK; col = e / kGK; } else { col = e % TN; kk = e / TN; }
+      const int gc = col0 + col, gk = kb + kk;
+      double v = 0.0;
+      if (gc < n && gk < kend) v = TB ? t.B[gc + (int64_t)gk * t.ldb] : t.B[gk + (int64_t)gc * t.ldb];
+      Bs[kk][col] = (MT)v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      MT a[MI], b[MJ];
+#pragma unroll
+      for (int i = 0; i < MI; ++i) a[i] = As[kk][r + 16 * i];
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) b[j] = Bs[kk][c + 16 * j];
+#pragma unroll
+      for (int i = 0; i < MI; ++i)
+#pragma unroll
+        for (int j = 0; j < MJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < MI; ++i)
+#pragma unroll
+    for (int j = 0; j < MJ; ++j) {
+      const int gr = row0 + r + 16 * i, gc = col0 + c + 16 * j;
+      if (gr < m && gc < n) {
+        double* p = t.C + gr + (int64_t)gc * t.ldc;
+        const double v = t.alpha * (double)acc[i][j];
+        if (atomic) atomicAdd(p, v);
+        else *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
+      }
+    }
+}
+
+template <bool TA, bool TB, typename MT>
 __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int atomic,
                                               double* fc) {
   const GemmTask t = tasks[blockIdx.y];
@@ -96,60 +161,23 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(k, kbeg + kchunk);
   if (kbeg >= kend && blockIdx.z > 0) return;
-  __shared__ double As[kGK][kGT + 1];
-  __shared__ double Bs[kGK][kGT + 1];
-  const int tid = threadIdx.x, r = tid & 15, c = tid >> 4;
-  double acc[4][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
-  for (int kb = kbeg; kb < kend; kb += kGK) {
-    for (int e = tid; e < kGT * kGK; e += 256) {
-      int row, kk;
-      if (!TA) { row = e % kGT; kk = e / kGT; } else { kk = e % kGK; row = e / kGK; }
-      const int gr = row0 + row, gk = kb + kk;
-      double v = 0.0;
-      if (gr < m && gk < kend) v = TA ? t.A[gk + (int64_t)gr * t.lda] : t.A[gr + (int64_t)gk * t.lda];
-      As[kk][row] = v;
-    }
-    for (int e = tid; e < kGT * kGK; e += 256) {
-      int col, kk;
-      if (!TB) { kk = e % kGK; col = e / kGK; } else { col = e % kGT; kk = e / kGT; }
-      const int gc = col0 + col, gk = kb + kk;
-      double v = 0.0;
-      if (gc < n && gk < kend) v = TB ? t.B[gc + (int64_t)gk * t.ldb] : t.B[gk + (int64_t)gc * t.ldb];
-      Bs[kk][col] = v;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kGK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][r + 16 * i];
-#pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][c + 16 * j];
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
-    }
-    __syncthreads();
+  __shared__ MT As[kGK][kGT + 1];
+  __shared__ MT Bs[kGK][kGT + 1];
+  const int em = min(kGT, m - row0), en = min(kGT, n - col0);
+  const int mi = em <= 16 ? 1 : (em <= 32 ? 2 : 4);
+  const int mj = en <= 16 ? 1 : (en <= 32 ? 2 : 4);
+  switch (mi * 8 + mj) {
+    case 9: gemm_tile<TA, TB, MT, 1, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 10: gemm_tile<TA, TB, MT, 1, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 12: gemm_tile<TA, TB, MT, 1, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 17: gemm_tile<TA, TB, MT, 2, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 18: gemm_tile<TA, TB, MT, 2, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 20: gemm_tile<TA, TB, MT, 2, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 33: gemm_tile<TA, TB, MT, 4, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 34: gemm_tile<TA, TB, MT, 4, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    default: gemm_tile<TA, TB, MT, 4, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
   }
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int gr = row0 + r + 16 * i, gc = col0 + c + 16 * j;
-      if (gr < m && gc < n) {
-        double* p = t.C + gr + (int64_t)gc * t.ldc;
-        const double v = t.alpha * acc[i][j];
-        if (atomic) atomicAdd(p, v);
-        else *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
-      }
-    }
-  if (fc && threadIdx.x == 0)
-    atomicAdd(fc, 2.0 * (double)min(kGT, m - row0) * (double)min(kGT, n - col0) * (double)max(kend - kbeg, 0));
+  if (fc && threadIdx.x == 0) atomicAdd(fc, 2.0 * (double)em * (double)en * (double)max(kend - kbeg, 0));
 }
 
 __global__ void k_axpby(const AxpbyTask* __restrict__ tasks) {
@@ -333,12 +361,20 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     DBuf d = upload(part, ctx->stream);
     dim3 grid(maxtiles, (unsigned)cnt, nz);
     const GemmTask* dt = d.as<GemmTask>();
-    double* fc = fc_ptr(ctx, ctx->gemm_kid);
-    ProfScope ps(ctx, ctx->gemm_kid);
-    if (!ta && !tb) k_gemm<false, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
-    else if (ta && !tb) k_gemm<true, false><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
-    else if (!ta && tb) k_gemm<false, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
-    else k_gemm<true, true><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, atomic ? 1 : 0, fc);
+    double* fc = fc_ptr(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
+    ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
+    const int at = atomic ? 1 : 0;
+    if (ctx->gemm_fp32) {
+      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+    } else {
+      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+    }
     check_launch("k_gemm");
   }
 }

@@ -30,12 +30,13 @@ namespace sp {
 
 // -------------------------------------------------------------------- tree --
 Tree::~Tree() {
-  if (d_lo) cudaFree(d_lo);
-  if (d_sz) cudaFree(d_sz);
+  if (d_lo) cudaFreeAsync(d_lo, stream);
+  if (d_sz) cudaFreeAsync(d_sz, stream);
 }
 
-std::shared_ptr<Tree> make_tree(int64_t n, int leaf) {
+std::shared_ptr<Tree> make_tree(int64_t n, int leaf, cudaStream_t stream) {
   auto t = std::make_shared<Tree>();
+  t->stream = stream;
   t->n = n;
   int L = 0;
   while ((n + (int64_t(1) << L) - 1) >> L > leaf) ++L;
@@ -55,10 +56,10 @@ std::shared_ptr<Tree> make_tree(int64_t n, int leaf) {
   int64_t mx = 0;
   for (int j = 0; j < (1 << L); ++j) mx = std::max(mx, t->sz[(1 << L) + j]);
   t->leaf_max = (int)mx;
-  check_cuda(cudaMalloc(&t->d_lo, sizeof(int64_t) * N), "tree alloc");
-  check_cuda(cudaMalloc(&t->d_sz, sizeof(int64_t) * N), "tree alloc");
-  check_cuda(cudaMemcpy(t->d_lo, t->lo.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice), "tree copy");
-  check_cuda(cudaMemcpy(t->d_sz, t->sz.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice), "tree copy");
+  t->d_lo = (int64_t*)dmalloc(sizeof(int64_t) * N, stream);
+  t->d_sz = (int64_t*)dmalloc(sizeof(int64_t) * N, stream);
+  check_cuda(cudaMemcpyAsync(t->d_lo, t->lo.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, stream), "tree copy");
+  check_cuda(cudaMemcpyAsync(t->d_sz, t->sz.data(), sizeof(int64_t) * N, cudaMemcpyHostToDevice, stream), "tree copy");
   return t;
 }
 
@@ -66,6 +67,7 @@ std::shared_ptr<Tree> make_tree(int64_t n, int leaf) {
 sp_hodlr* hodlr_alloc(sp_ctx* ctx, std::shared_ptr<Tree> tree, int cap, double tol) {
   auto* M = new sp_hodlr;
   M->tree = tree;
+  M->stream = ctx->stream;
   M->cap = cap;
   M->tol = tol;
   M->leaf_ld = tree->leaf_max;
@@ -84,15 +86,15 @@ sp_hodlr* hodlr_alloc(sp_ctx* ctx, std::shared_ptr<Tree> tree, int cap, double t
   return M;
 }
 
+// Stream-ordered release on the allocation stream: work already enqueued on
+// that stream that reads the matrix completes first.
 void hodlr_free(sp_hodlr* M) {
   if (!M) return;
-  // frees are stream-ordered on the legacy stream: wait for all work first
-  cudaDeviceSynchronize();
-  if (M->leaves) cudaFree(M->leaves);
-  if (M->U) cudaFree(M->U);
-  if (M->V) cudaFree(M->V);
-  if (M->rank) cudaFree(M->rank);
-  if (M->band) cudaFree(M->band);
+  dfree(M->leaves, M->stream);
+  dfree(M->U, M->stream);
+  dfree(M->V, M->stream);
+  dfree(M->rank, M->stream);
+  dfree(M->band, M->stream);
   delete M;
 }
 
@@ -275,7 +277,7 @@ __global__ void k_max_rank(const int* __restrict__ rank, int N, int* out) {
 
 sp_hodlr* hodlr_from_band(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, int leaf,
                           double tol, int cap) {
-  auto tree = make_tree(n, leaf);
+  auto tree = make_tree(n, leaf, ctx->stream);
   sp_hodlr* M = hodlr_alloc(ctx, tree, cap, tol);
   try {
     M->b = b;

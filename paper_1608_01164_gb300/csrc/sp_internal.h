@@ -28,6 +28,7 @@
 namespace sp {
 
 struct Tree {
+  cudaStream_t stream = nullptr;  // stream its device arrays were allocated on
   int64_t n = 0;
   int L = 0;         // depth; leaves at level L
   int leaf_max = 0;  // largest leaf size
@@ -40,7 +41,7 @@ struct Tree {
   static int level_of(int c) { return 31 - __builtin_clz((unsigned)c); }
 };
 
-std::shared_ptr<Tree> make_tree(int64_t n, int leaf);
+std::shared_ptr<Tree> make_tree(int64_t n, int leaf, cudaStream_t stream);
 // Two HODLR matrices can be combined when their partitions coincide.
 inline bool same_tree(const Tree& a, const Tree& b) { return a.n == b.n && a.L == b.L && a.lo == b.lo; }
 
@@ -48,6 +49,7 @@ inline bool same_tree(const Tree& a, const Tree& b) { return a.n == b.n && a.L =
 
 struct sp_hodlr {
   std::shared_ptr<sp::Tree> tree;
+  cudaStream_t stream = nullptr;  // allocation stream: buffers are freed stream-ordered on it
   int cap = 0;
   double tol = 0.0;
   int leaf_ld = 0;
@@ -74,7 +76,7 @@ namespace sp {
 // Kernel families timed and flop-counted by the profiler.
 enum KernelId {
   KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_JACOBI, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
-  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_COUNT
+  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_COUNT
 };
 }  // namespace sp
 
@@ -89,6 +91,7 @@ struct sp_ctx {
   // algorithmic flops the kernels count themselves (d_fc[kid])
   bool profiling = false;
   int gemm_kid = sp::KID_GEMM;  // profiler bucket of k_gemm launches (call site)
+  bool gemm_fp32 = false;       // mixed-precision scope: k_gemm computes in binary32
   double* d_fc = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
   int64_t launches[sp::KID_COUNT] = {};
@@ -125,6 +128,13 @@ struct GemmSite {
   int prev;
   GemmSite(sp_ctx* c, int kid) : ctx(c), prev(c->gemm_kid) { ctx->gemm_kid = kid; }
   ~GemmSite() { ctx->gemm_kid = prev; }
+};
+// Binary32 GEMM arithmetic inside a scope (mixed-precision steps).
+struct Fp32Gemms {
+  sp_ctx* ctx;
+  bool prev;
+  explicit Fp32Gemms(sp_ctx* c) : ctx(c), prev(c->gemm_fp32) { ctx->gemm_fp32 = true; }
+  ~Fp32Gemms() { ctx->gemm_fp32 = prev; }
 };
 // Device flop counter of a family (null unless profiling).
 inline double* fc_ptr(sp_ctx* ctx, int kid) { return ctx->profiling ? ctx->d_fc + kid : nullptr; }
