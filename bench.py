@@ -8,9 +8,12 @@ Default workload: tridiagonal n = 100000, off-diagonal -1, diagonal i.i.d.
 U[-0.5, 0.5], nu = n/2 (mu between lambda_nu and lambda_nu+1), leaf 256,
 tol 1e-10, binary64.  `--workload band4`: b = 4 with N(0,1) entries.
 
-Multi-GPU: one process per GPU (torchrun); a single projector does not shard,
-so every rank computes an independent replica (its own seed) and the job's
-value is the max step time over ranks divided by the number of ranks.
+Multi-GPU: one process per GPU (torchrun).  A single projector does not
+shard, so every rank computes an independent replica (its own seed) and the
+job's value is the max step time over ranks divided by the number of ranks.
+`--workload batched` partitions the instances across ranks (longest first,
+greedy by estimated cost), with no collective on the data path; the value is
+all instances over the max wall time over ranks.
 
 --impl reference: the CPU oracle (dense eigensolver projector) timed on the
 host on a bounded sample of the same workload, scaled to the metric's unit.
@@ -36,7 +39,7 @@ METRIC = "s/projector at n=1e5 & batched projectors/s; mixed vs FP64 GPU at â€–Î
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 binary64 rate (1.203 measured by a DFMA loop on this machine)
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=3)
@@ -53,7 +56,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample-n", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    return p.parse_args(argv)
 
 
 def workload_band(args, rank):
@@ -78,6 +81,44 @@ def config_dict(args, name, ab, nu):
             "l2": "flushed between steps (256 MiB write); working set (GBs) exceeds L2"}
 
 
+# ------------------------------------------------------------ multi-rank ----
+
+def rank_env():
+    """(world, rank, local_rank) from the launcher's environment."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """Max of a per-rank scalar over all ranks (identity at world 1)."""
+    if world <= 1 or x is None:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def shard_instances(costs, world):
+    """Partition instance indices over ranks: longest first, each to the rank
+    with the least estimated cost so far (ties to the lowest rank).  Every
+    rank computes the same partition from the same costs."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    parts = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda q: (load[q], q))
+        parts[r].append(i)
+        load[r] += costs[i]
+    return parts
+
+
+def instance_cost(n, b):
+    """Relative cost estimate of one projector: HODLR work ~ n (b + log n)^2."""
+    return n * (b + np.log2(max(n, 2))) ** 2
+
+
 # ------------------------------------------------------------ CPU oracle ----
 
 def cpu_oracle_sample(args, ab_full, nu_full, reps=1):
@@ -100,7 +141,7 @@ def cpu_oracle_sample(args, ab_full, nu_full, reps=1):
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    _, rank, _ = rank_env()
     if rank != 0:
         return 0
     name, ab, nu = workload_band(args, 0)
@@ -185,9 +226,7 @@ def run_ours(args):
 
     import paper_1608_01164_gb300 as sp
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
@@ -247,11 +286,7 @@ def run_ours(args):
     prof = sp.sp_ctx_profile(ctx)
     sp.sp_ctx_set_profiling(ctx, False)
     ms = [a.elapsed_time(b) for a, b in ev]
-    step_ms = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
+    step_ms = max_over_ranks(float(np.mean(ms)), world, "cuda")
     # end to end through the C ABI: host band in, trace out
     ab_host = np.ascontiguousarray(ab)
     e2e = []
@@ -261,11 +296,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         tr, _ = step(ab_host)
         e2e.append(time.perf_counter() - t0)
-    e2e_s = float(np.mean(e2e)) if e2e else None
-    if world > 1 and e2e_s is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(float(np.mean(e2e)) if e2e else None, world, "cuda")
     # dominant kernel by device time; the k_gemm call-site buckets are one kernel
     per_kernel = {}
     for k, (la, ms_k, fl) in prof.items():
@@ -315,15 +346,29 @@ def run_ours(args):
 
 def run_batched(args):
     """Workload 3: independent instances (n log-uniform in [512, 8192], b in
-    {1,2,4,8}, U[-1,1], nu in {n/3, n/2}); metric projectors/s."""
+    {1,2,4,8}, U[-1,1], nu in {n/3, n/2}); metric projectors/s.  Under
+    torchrun each rank takes its share of the instances."""
     import torch
+    import torch.distributed as dist
 
     import paper_1608_01164_gb300 as sp
 
-    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    world, rank, local = rank_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
     sp.load()
     ctx = sp.sp_ctx_create(0)
-    inst = sp_inputs.workload(3, n=args.batch)
+    everything = sp_inputs.workload(3, n=args.batch)
+    mine = shard_instances([instance_cost(ab.shape[0], ab.shape[1] - 1) for _, ab, _ in everything], world)[rank]
+    inst = [everything[i] for i in mine]
     mus = [sp.sp_locate_shift(ctx, ab, nu)[0] for _, ab, nu in inst]
     bands = [torch.from_numpy(np.ascontiguousarray(ab)).cuda() for _, ab, _ in inst]
 
@@ -338,22 +383,30 @@ def run_batched(args):
         trs, infos = step()
     bad = sum(1 for (_, _, nu), t in zip(inst, trs) if round(t) != nu)
     l0 = sp.sp_launch_count()
+    barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
         trs, infos = step()
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / args.steps
-    line = {"metric": METRIC, "value": len(inst) / dt, "unit": "projectors/s", "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * dt, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"batched: {len(inst)} instances, n log-uniform [512, 8192], b in {{1,2,4,8}}, "
-                                   f"U[-1,1], nu in {{n/3, n/2}}, leaf auto, tol {args.tol:g}, {args.nstreams} streams",
-                       "l2": "working set exceeds L2"},
-            "gpu_launches": int(sp.sp_launch_count() - l0), "trace_mismatches": bad,
-            "timing": "host wall clock around whole batches (the batch call synchronises)"}
-    print(json.dumps(line), flush=True)
+    dt = max_over_ranks((time.perf_counter() - t0) / args.steps, world, "cuda")
+    launches = sp.sp_launch_count() - l0
+    bad = int(max_over_ranks(bad, world, "cuda") if world > 1 else bad)
     sp.sp_ctx_destroy(ctx)
+    if rank == 0:
+        line = {"metric": METRIC, "value": len(everything) / dt, "unit": "projectors/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt, "higher_is_better": True,
+                "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": f"batched: {len(everything)} instances, n log-uniform [512, 8192], "
+                                       f"b in {{1,2,4,8}}, U[-1,1], nu in {{n/3, n/2}}, leaf auto, tol {args.tol:g}, "
+                                       f"{args.nstreams} streams per GPU",
+                           "l2": "working set exceeds L2"},
+                "gpu_launches": int(launches), "trace_mismatches": bad,
+                "timing": "host wall clock around whole batches (the batch call synchronises), max over ranks"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
     return 0
 
 
