@@ -46,7 +46,7 @@ def parse(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="tridiag", choices=["tridiag", "band4", "band16", "batched"])
-    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    p.add_argument("--precision", default="fp64", choices=["fp64", "mixed", "mixed-ns"])
     p.add_argument("--polish", type=int, default=1)
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--nstreams", type=int, default=16)
@@ -76,7 +76,7 @@ def workload_band(args, rank):
 
 def config_dict(args, name, ab, nu):
     return {"workload": f"{name} n={args.n} b={ab.shape[1] - 1} nu={nu} leaf={args.leaf} tol={args.tol:g} "
-                        f"{args.precision}" + (f" polish={args.polish}" if args.precision == "mixed" else ""),
+                        f"{args.precision}" + (f" polish={args.polish}" if args.precision != "fp64" else ""),
             "n": args.n, "b": ab.shape[1] - 1, "nu": nu, "leaf": args.leaf, "tol": args.tol,
             "l2": "flushed between steps (256 MiB write); working set (GBs) exceeds L2"}
 
@@ -246,8 +246,8 @@ def run_ours(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     opts = sp.sp_qdwh_opts_default()
-    if args.precision == "mixed":
-        opts.precision = sp.SP_MIXED_FP32
+    if args.precision != "fp64":
+        opts.precision = sp.SP_MIXED_FP32 if args.precision == "mixed" else sp.SP_MIXED_NS
         opts.polish_steps = args.polish
 
     def step(band):
@@ -284,6 +284,9 @@ def run_ours(args):
     clocks = sampler.stop()
     launches = sp.sp_launch_count() - l0
     prof = sp.sp_ctx_profile(ctx)
+    chol_levels = [round(float(v) / args.steps, 2) for v in sp.sp_ctx_profile_levels(ctx, 24)]
+    while chol_levels and chol_levels[-1] == 0.0:
+        chol_levels.pop()
     sp.sp_ctx_set_profiling(ctx, False)
     ms = [a.elapsed_time(b) for a, b in ev]
     step_ms = max_over_ranks(float(np.mean(ms)), world, "cuda")
@@ -300,6 +303,8 @@ def run_ours(args):
     # dominant kernel by device time; the k_gemm call-site buckets are one kernel
     per_kernel = {}
     for k, (la, ms_k, fl) in prof.items():
+        if k == "host_wait":  # host time blocked at syncs, not a kernel
+            continue
         base = k.split("[")[0]
         a = per_kernel.setdefault(base, [0, 0.0, 0.0])
         a[0] += la
@@ -335,6 +340,7 @@ def run_ours(args):
                        "alpha": info.alpha, "l0": info.l0, "ms_polish": info.ms_polish,
                        "ms_param": info.ms_param, "ms_qr": info.ms_qr, "ms_chol": info.ms_chol,
                        "trace_minus_nu": traces[-1] - nu, "wall_s": t_wall,
+                       "chol_self_ms_per_level": chol_levels,
                        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "gflop": round(v[2] / 1e9, 3)}
                                    for k, v in prof.items() if v[0]}}}
     print(json.dumps(line), flush=True)

@@ -53,6 +53,14 @@ extern "C" {
                             X + (a-1) X Z^{-1} (I - X^2) with binary32 GEMM
                             arithmetic (binary64 storage, residual, sum and
                             recompression), then binary64 Newton-Schulz polish */
+#define SP_MIXED_NS 2    /* once 1 - l_k^2 <= 1e-2 the remaining QDWH steps are
+                            replaced by Newton-Schulz steps in residual form
+                            X + X (I - X^2)/2: I - X^2 in binary64, the product
+                            X (I - X^2) with binary32 GEMM arithmetic, as many
+                            steps as the scalar map l <- l(3 - l^2)/2 needs to
+                            reach 1 - l <= 1e-12; then the binary64 polish.
+                            No H-Cholesky in the late steps (not the paper's
+                            iteration; a growth direction). */
 
 typedef struct sp_ctx* sp_ctx_t;
 typedef struct sp_hodlr* sp_hodlr_t;
@@ -61,7 +69,7 @@ typedef struct sp_hodlr* sp_hodlr_t;
 typedef struct {
   int max_iter;      /* hard cap on QDWH iterations (default 10) */
   double delta;      /* stopping tolerance: stop when |1 - l_k| <= delta (default 1e-15) */
-  int precision;     /* SP_FP64 (default) or SP_MIXED_FP32 */
+  int precision;     /* SP_FP64 (default), SP_MIXED_FP32 or SP_MIXED_NS */
   int polish_steps;  /* binary64 Newton-Schulz steps X <- X (3I - X^2)/2 after a mixed run (default 1) */
   double alpha;      /* > 0: use as the bound alpha >= ||A - mu I||_2; 0: estimate it */
   double l0;         /* > 0: use as the bound l0 <= sigma_min(X_0); 0: estimate it */
@@ -73,7 +81,7 @@ typedef struct {
   int iters;               /* QDWH iterations performed */
   double alpha, l0;        /* the parameters used */
   double l[16], a[16], b[16], c[16]; /* l_k, a_k, b_k, c_k per iteration */
-  int kind[16];            /* 1 = QR-based step, 2 = Cholesky-based step, 3 = mixed residual step */
+  int kind[16];            /* 1 = QR-based, 2 = Cholesky-based, 3 = mixed residual, 4 = mixed Newton-Schulz step */
   int max_rank;            /* largest off-diagonal rank of the result */
   size_t bytes;            /* device bytes held by the result */
   double ms_param, ms_qr, ms_chol, ms_total; /* phase times (CUDA events) */
@@ -110,6 +118,15 @@ int sp_ctx_set_profiling(sp_ctx_t ctx, int on);
  * flops of kernel family `kernel` (0 <= kernel < sp_kernel_count()) since the
  * last reset.  Synchronising. */
 int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, double* flops);
+
+/* Per-tree-level self time (ms) of the H-Cholesky recursion while profiling
+ * is on: for each node, the time of its own work on the context's stream
+ * (Schur complement and inverse blocks for inner nodes, factor and inverse for
+ * leaves), excluding its children, summed over the nodes of each level
+ * 0..nlevels-1 and over every factorisation since profiling was enabled.
+ * Synchronises the context's stream.  Measurement hook; the paper has no
+ * counterpart.  Returns SP_EINVAL for nlevels < 0 or a NULL array. */
+int sp_ctx_profile_levels(sp_ctx_t ctx, int nlevels, double* ms_self);
 /* Name of a kernel family ("k_gemm", "k_qr", ...), "" if out of range. */
 const char* sp_kernel_name(int kernel);
 int sp_kernel_count(void);

@@ -24,7 +24,7 @@ SOURCES = ["sp_blas.cu", "sp_lowrank.cu", "sp_hodlr.cu", "sp_qrstep.cu", "sp_par
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 
 SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_EBREAKDOWN, SP_ENONFINITE, SP_ERANK, SP_ETIMEOUT, SP_EINTERNAL = range(9)
-SP_FP64, SP_MIXED_FP32 = 0, 1
+SP_FP64, SP_MIXED_FP32, SP_MIXED_NS = 0, 1, 2
 SP_NOALLOC_SCRATCH_DOUBLES = 1 << 20
 
 # every entry point declared in include/sp.h
@@ -33,7 +33,7 @@ EXPORTS = [
     "sp_hodlr_from_band", "sp_qdwh_sign", "sp_projector", "sp_apply", "sp_to_dense", "sp_trace",
     "sp_hodlr_info", "sp_hodlr_destroy", "sp_hodlr_add", "sp_hodlr_mult", "sp_hodlr_cholesky",
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
-    "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_kernel_name", "sp_kernel_count",
+    "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
     "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector",
 ]
 
@@ -118,6 +118,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_fastqr_factors": (I, [P, P, D, PP, PP]),
         "sp_ctx_set_profiling": (I, [P, I]),
         "sp_ctx_profile": (I, [P, I, ctypes.POINTER(I64), ctypes.POINTER(D), ctypes.POINTER(D)]),
+        "sp_ctx_profile_levels": (I, [P, I, ctypes.c_void_p]),
         "sp_kernel_name": (ctypes.c_char_p, [I]),
         "sp_kernel_count": (I, []),
         "sp_launch_count": (I64, []),
@@ -311,6 +312,14 @@ def sp_ctx_profile(ctx):
         la, ms, fl = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
         _check(ctx, _lib.sp_ctx_profile(ctx, k, ctypes.byref(la), ctypes.byref(ms), ctypes.byref(fl)))
         out[_lib.sp_kernel_name(k).decode()] = (la.value, ms.value, fl.value)
+    return out
+
+
+def sp_ctx_profile_levels(ctx, nlevels: int = 32):
+    """Per-tree-level self time (ms) of the H-Cholesky nodes while profiling."""
+    import numpy as _np
+    out = _np.zeros(nlevels)
+    _check(ctx, _lib.sp_ctx_profile_levels(ctx, nlevels, out.ctypes.data))
     return out
 
 

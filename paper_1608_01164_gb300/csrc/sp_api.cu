@@ -81,7 +81,13 @@ DBuf band_on_device(sp_ctx* ctx, int64_t n, int b, const double* ab, int64_t lda
 int read_flags(sp_ctx* ctx) {
   int h[NFLAGS];
   check_cuda(cudaMemcpyAsync(h, ctx->d_flags, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "flags");
+  const auto t0 = std::chrono::steady_clock::now();
   check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  if (ctx->profiling) {
+    // host time blocked here: the device was still busy with enqueued work
+    ctx->ms[KID_HOST_WAIT] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    ctx->launches[KID_HOST_WAIT] += 1;
+  }
   if (h[FLAG_RANK]) return SP_ERANK;
   if (h[FLAG_BREAKDOWN]) return SP_EBREAKDOWN;
   if (h[FLAG_NONFINITE]) return SP_ENONFINITE;
@@ -223,6 +229,32 @@ sp_hodlr* newton_schulz_step(sp_ctx* ctx, const sp_hodlr* X) {
   return Xn.release();
 }
 
+// Newton-Schulz step in residual form with the correction product in binary32
+// GEMM arithmetic: R = I - X^2 (binary64), D = X R (binary32 GEMMs, binary64
+// storage and recompression), X <- X + D/2 (binary64).  The binary32 rounding
+// error scales with ||R||, which the iteration drives to zero.
+sp_hodlr* newton_schulz_step_mixed(sp_ctx* ctx, const sp_hodlr* X, sp_info* inf) {
+  Timer t1(ctx->stream);
+  Owned XX(hodlr_mult(ctx, X, X));
+  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0));
+  XX.reset(nullptr);
+  inf->ms_mult += t1.stop();
+  Owned D(nullptr);
+  {
+    Fp32Gemms fp32(ctx);
+    Timer t2(ctx->stream);
+    D.reset(hodlr_mult(ctx, X, R.p));
+    inf->ms_solve += t2.stop();
+  }
+  R.reset(nullptr);
+  Timer t3(ctx->stream);
+  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0));
+  D.reset(nullptr);
+  hodlr_symmetrize(ctx, Xn.p);
+  inf->ms_combine += t3.stop();
+  return Xn.release();
+}
+
 // QR-based first step on the band kept by A (A = A - mu I in HODLR)
 sp_hodlr* qr_step(sp_ctx* ctx, const sp_hodlr* A, double alpha, double a, double b, double c) {
   const double sc = std::sqrt(c);
@@ -267,6 +299,14 @@ int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
     check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
     check_cuda(cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS), "flags");
     check_cuda(cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS), "flags");
+    // Every formatted operation allocates and frees its temporaries in stream
+    // order from the device's default pool.  Keep freed memory in the pool
+    // across synchronisations (the default threshold 0 hands it back to the
+    // driver at every sync, and the next step maps it again).  Per process.
+    cudaMemPool_t pool;
+    check_cuda(cudaDeviceGetDefaultMemPool(&pool, ctx->device), "default mem pool");
+    uint64_t keep = UINT64_MAX;
+    check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "mem pool threshold");
   });
   if (rc != SP_OK) {
     delete ctx;
@@ -311,6 +351,10 @@ int sp_ctx_set_profiling(sp_ctx_t ctx, int on) {
       ctx->launches[k] = 0;
       ctx->ms[k] = 0.0;
     }
+    for (auto& ne : ctx->chol_ev)
+      for (int k = 0; k < ne.nev; ++k) cudaEventDestroy(ne.e[k]);
+    ctx->chol_ev.clear();
+    for (double& v : ctx->chol_level_ms) v = 0.0;
     ctx->profiling = on != 0;
   });
 }
@@ -337,11 +381,31 @@ int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, doub
   });
 }
 
+int sp_ctx_profile_levels(sp_ctx_t ctx, int nlevels, double* ms_self) {
+  if (!ctx || nlevels < 0 || (nlevels > 0 && !ms_self)) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    for (auto& ne : ctx->chol_ev) {
+      float a = 0.f, b = 0.f;
+      if (ne.nev == 2) {
+        check_cuda(cudaEventElapsedTime(&a, ne.e[0], ne.e[1]), "event time");
+      } else if (ne.nev == 5) {
+        check_cuda(cudaEventElapsedTime(&a, ne.e[1], ne.e[2]), "event time");
+        check_cuda(cudaEventElapsedTime(&b, ne.e[3], ne.e[4]), "event time");
+      }
+      if (ne.level >= 0 && ne.level < 64) ctx->chol_level_ms[ne.level] += (double)a + (double)b;
+      for (int k = 0; k < ne.nev; ++k) cudaEventDestroy(ne.e[k]);
+    }
+    ctx->chol_ev.clear();
+    for (int l = 0; l < nlevels; ++l) ms_self[l] = l < 64 ? ctx->chol_level_ms[l] : 0.0;
+  });
+}
+
 const char* sp_kernel_name(int kernel) {
-  static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_jacobi_svd", "k_gather",
+  static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_core_svd", "k_gather",
                                          "k_leaf_potrf", "k_leaf_trsm", "k_givens", "k_replay_leaf",
                                          "k_replay_track", "k_inertia", "misc", "k_gemm[apply]",
-                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm[fp32]"};
+                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm[fp32]", "host_wait"};
   return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
 }
 
@@ -369,7 +433,8 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
   sp_qdwh_opts_default(&o);
   if (opts_in) o = *opts_in;
   if (o.max_iter < 1 || o.max_iter > 16 || !(o.delta > 0.0) || o.qr_steps < 0 || o.qr_steps > 1 ||
-      (o.precision != SP_FP64 && o.precision != SP_MIXED_FP32) || o.polish_steps < 0 || o.polish_steps > 4) {
+      (o.precision != SP_FP64 && o.precision != SP_MIXED_FP32 && o.precision != SP_MIXED_NS) ||
+      o.polish_steps < 0 || o.polish_steps > 4) {
     ctx->err = "sp_qdwh_sign: invalid options (max_iter in 1..16, delta > 0, qr_steps in {0, 1}, precision, "
                "polish_steps in 0..4)";
     return SP_EINVAL;
@@ -415,8 +480,30 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
       l = l * (a + bb * l2) / (1.0 + c * l2);
     }
     Owned X(nullptr);
-    const int K = (int)as.size();
+    int K = (int)as.size();
     for (int k = 0; k < K; ++k) {
+      if (o.precision == SP_MIXED_NS && k > 0 && (1.0 - ls[k] * ls[k]) <= kMixedThreshold) {
+        // the remaining QDWH steps are replaced by Newton-Schulz steps,
+        // counted by the scalar map on l until 1 - l <= 1e-12
+        if (!X.p) X.reset(hodlr_add(ctx, 1.0 / alpha, A, 0.0, nullptr, 0.0));
+        double lns = ls[k];
+        int s = k;
+        while (1.0 - lns > 1e-12 && s < 16) {
+          Timer t(ctx->stream);
+          inf.l[s] = lns;
+          inf.a[s] = 1.5;
+          inf.b[s] = -0.5;
+          inf.c[s] = 0.0;
+          X.reset(newton_schulz_step_mixed(ctx, X.p, &inf));
+          inf.kind[s] = 4;
+          check_flags(ctx, "Newton-Schulz step");
+          inf.ms_chol += t.stop();
+          lns = 0.5 * lns * (3.0 - lns * lns);
+          ++s;
+        }
+        K = s;
+        break;
+      }
       inf.l[k] = ls[k];
       inf.a[k] = as[k];
       inf.b[k] = bs[k];
@@ -443,7 +530,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
         inf.ms_chol += t.stop();
       }
     }
-    if (o.precision == SP_MIXED_FP32 && X.p) {
+    if (o.precision != SP_FP64 && X.p) {
       Timer t(ctx->stream);
       for (int p = 0; p < o.polish_steps; ++p) X.reset(newton_schulz_step(ctx, X.p));
       check_flags(ctx, "Newton-Schulz polish");

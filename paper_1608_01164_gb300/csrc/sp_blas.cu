@@ -319,6 +319,82 @@ __global__ void __launch_bounds__(256) k_leaf_trsm(const LeafTask* __restrict__ 
     __syncthreads();
   }
 }
+
+// Li = L^{-1} for a lower-triangular leaf L (n <= kInvRows * 256).  CTA =
+// (block of kInvCols identity columns, task); forward substitution L X = I
+// restricted to those columns, which are zero above their first column c0,
+// so the sweep starts at step c0.  Thread t owns rows t, t + 256, ...; its
+// entries of the block stay in registers, and one pivot row per step goes
+// through shared memory (double-buffered: one barrier per step).  Many
+// small CTAs per leaf spread the n^3/3 flops over many SMs.
+constexpr int kInvCols = 4;
+constexpr int kInvRows = 4;
+
+__global__ void __launch_bounds__(256) k_leaf_inv(const LeafTask* __restrict__ tasks) {
+  const LeafTask t = tasks[blockIdx.y];
+  const int n = t.n;
+  const int c0 = blockIdx.x * kInvCols;
+  if (c0 >= n) return;
+  const double* L = t.A;
+  const int64_t lda = t.lda;
+  __shared__ double dinv[kInvRows * 256];
+  __shared__ double piv[2][kInvCols];
+  for (int j = c0 + threadIdx.x; j < n; j += blockDim.x) dinv[j] = 1.0 / L[j + (int64_t)j * lda];
+  double x[kInvRows][kInvCols];
+#pragma unroll
+  for (int r = 0; r < kInvRows; ++r)
+#pragma unroll
+    for (int c = 0; c < kInvCols; ++c) x[r][c] = (threadIdx.x + 256 * r == c0 + c) ? 1.0 : 0.0;
+  double lcur[kInvRows];
+#pragma unroll
+  for (int r = 0; r < kInvRows; ++r) {
+    const int i = threadIdx.x + 256 * r;
+    lcur[r] = (i < n) ? L[i + (int64_t)c0 * lda] : 0.0;
+  }
+  __syncthreads();
+  for (int j = c0; j < n; ++j) {
+    const int owner = j & 255, slot = j >> 8;
+    if (threadIdx.x == owner) {
+      const double di = dinv[j];
+#pragma unroll
+      for (int r = 0; r < kInvRows; ++r)
+        if (r == slot) {
+#pragma unroll
+          for (int c = 0; c < kInvCols; ++c) {
+            x[r][c] *= di;
+            piv[j & 1][c] = x[r][c];
+          }
+        }
+    }
+    __syncthreads();
+    double lnext[kInvRows];
+#pragma unroll
+    for (int r = 0; r < kInvRows; ++r) {
+      const int i = threadIdx.x + 256 * r;
+      lnext[r] = (j + 1 < n && i < n) ? L[i + (int64_t)(j + 1) * lda] : 0.0;
+    }
+    double p[kInvCols];
+#pragma unroll
+    for (int c = 0; c < kInvCols; ++c) p[c] = piv[j & 1][c];
+#pragma unroll
+    for (int r = 0; r < kInvRows; ++r) {
+      const int i = threadIdx.x + 256 * r;
+      if (i > j && i < n) {
+#pragma unroll
+        for (int c = 0; c < kInvCols; ++c) x[r][c] = fma(-lcur[r], p[c], x[r][c]);
+      }
+      lcur[r] = lnext[r];
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kInvRows; ++r) {
+    const int i = threadIdx.x + 256 * r;
+    if (i < n)
+#pragma unroll
+      for (int c = 0; c < kInvCols; ++c)
+        if (c0 + c < n) t.X[i + (int64_t)(c0 + c) * t.ldx] = x[r][c];
+  }
+}
 }  // namespace
 
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, bool atomic, int ksplit) {
@@ -437,6 +513,24 @@ void leaf_trsm(sp_ctx* ctx, bool trans, const std::vector<LeafTask>& tasks) {
     if (trans) k_leaf_trsm<true><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
     else k_leaf_trsm<false><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
     check_launch("k_leaf_trsm");
+  }
+}
+
+void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
+  if (tasks.empty()) return;
+  int maxn = 0;
+  for (const auto& t : tasks) {
+    if (t.n > kInvRows * 256) fail(SP_EINVAL, "leaf inverse: leaf larger than 1024 rows");
+    maxn = std::max(maxn, t.n);
+  }
+  for (size_t off = 0; off < tasks.size(); off += 65535) {
+    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
+    std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
+    DBuf d = upload(part, ctx->stream);
+    dim3 grid((maxn + kInvCols - 1) / kInvCols, (unsigned)cnt);
+    ProfScope ps(ctx, KID_TRSM);
+    k_leaf_inv<<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
+    check_launch("k_leaf_inv");
   }
 }
 

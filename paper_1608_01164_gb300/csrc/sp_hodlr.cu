@@ -679,21 +679,16 @@ static void lr_update_sub(sp_ctx* ctx, sp_hodlr* M, int c, const double* Ul, int
 }
 
 // ------------------------------------------------------- leaf inverses ------
-// Li_leaf = L_leaf^{-1} for lower-triangular leaves (identity, then a leaf
-// forward substitution with n right-hand sides).
+// Li_leaf = L_leaf^{-1} for lower-triangular leaves.
 static void leaf_inverse(sp_ctx* ctx, const sp_hodlr* Lf, sp_hodlr* Li, const std::vector<int>& leaves) {
   const Tree& T = *Lf->tree;
-  std::vector<AxpbyTask> id;
   std::vector<LeafTask> tr;
   for (int c : leaves) {
     const int jl = c - (1 << T.L);
     const int s = (int)T.sz[c];
-    id.push_back(AxpbyTask{nullptr, Li->leaf(jl), 0, Li->leaf_ld, Li->leaf_ld, Li->leaf_ld, nullptr, nullptr, 0.0,
-                           0.0, 1.0});
     tr.push_back(LeafTask{Lf->leaf(jl), Lf->leaf_ld, s, Li->leaf(jl), Li->leaf_ld, s, nullptr});
   }
-  axpby_batched(ctx, id);
-  leaf_trsm(ctx, false, tr);
+  leaf_inverse_batched(ctx, tr);
 }
 
 // Lower block of the inverse at the right child c2 of a factored node:
@@ -753,17 +748,38 @@ sp_hodlr* hodlr_tri_inverse(sp_ctx* ctx, const sp_hodlr* Lf) {
 // right subtree, right subtree), carrying the inverse factor Li = L^{-1}
 // along so that every triangular solve with a factored subtree is a parallel
 // HODLR-times-skinny product instead of a chain of leaf substitutions.
+// Profiler hook: records an event on the context's stream into slot k of
+// the node's event set (no-op unless profiling).
+static void node_mark(sp_ctx* ctx, long idx, int k) {
+  if (idx < 0) return;
+  auto& ne = ctx->chol_ev[idx];
+  check_cuda(cudaEventCreate(&ne.e[k]), "event");
+  check_cuda(cudaEventRecord(ne.e[k], ctx->stream), "event record");
+  ne.nev = k + 1;
+}
+
+static long node_open(sp_ctx* ctx, int level) {
+  if (!ctx->profiling) return -1;
+  ctx->chol_ev.push_back(sp_ctx::NodeEvents{level, 0, {}});
+  const long idx = (long)ctx->chol_ev.size() - 1;
+  node_mark(ctx, idx, 0);
+  return idx;
+}
+
 static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, sp_hodlr* Li, int c, double* tmp, double* G, double* UG) {
   const Tree& T = *Lf->tree;
+  const long pe = node_open(ctx, Tree::level_of(c));
   if (Tree::level_of(c) == T.L) {
     const int jl = c - (1 << T.L);
     leaf_potrf(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], nullptr, 0, 0, nullptr}});
     leaf_inverse(ctx, Lf, Li, {c});
+    node_mark(ctx, pe, 1);
     return;
   }
   const int c1 = 2 * c, c2 = 2 * c + 1;
   GemmSite site(ctx, KID_GEMM_CHOL);
   chol_rec(ctx, Lf, Li, c1, tmp, G, UG);
+  node_mark(ctx, pe, 1);
   // L21 = Z21 L11^{-T} = U (L11^{-1} V)^T: V_{c2} <- Li_sub(c1) V_{c2}
   hodlr_apply_sub(ctx, Li, c1, Lf->Vc(c2), T.n, tmp, T.sz[c1], Lf->cap, Lf->rank + c2, false, false);
   check_cuda(cudaMemcpy2DAsync(Lf->Vc(c2), T.n * sizeof(double), tmp, T.sz[c1] * sizeof(double),
@@ -782,8 +798,11 @@ static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, sp_hodlr* Li, int c, double* tmp
   check_launch("k_set_int");
   zero_tail_batched(ctx, {ZeroTailTask{Lf->Uc(c1), T.n, (int)T.sz[c1], Lf->rank + c1, Lf->cap},
                           ZeroTailTask{Lf->Vc(c1), T.n, (int)T.sz[c2], Lf->rank + c1, Lf->cap}});
+  node_mark(ctx, pe, 2);
   chol_rec(ctx, Lf, Li, c2, tmp, G, UG);
+  node_mark(ctx, pe, 3);
   inverse_blocks(ctx, Lf, Li, {c2});
+  node_mark(ctx, pe, 4);
 }
 
 void hodlr_cholesky_inv(sp_ctx* ctx, const sp_hodlr* Z, sp_hodlr** Lout, sp_hodlr** Liout) {

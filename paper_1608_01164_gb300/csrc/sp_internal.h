@@ -75,8 +75,8 @@ struct sp_hodlr {
 namespace sp {
 // Kernel families timed and flop-counted by the profiler.
 enum KernelId {
-  KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_JACOBI, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
-  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_COUNT
+  KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_CORE_SVD, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
+  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_HOST_WAIT, KID_COUNT
 };
 }  // namespace sp
 
@@ -96,6 +96,15 @@ struct sp_ctx {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
   int64_t launches[sp::KID_COUNT] = {};
   double ms[sp::KID_COUNT] = {};
+  // H-Cholesky nodes: events bracketing each node's own work (not its
+  // children's), folded into per-tree-level self times when read
+  struct NodeEvents {
+    int level;
+    int nev;
+    cudaEvent_t e[5];
+  };
+  std::vector<NodeEvents> chol_ev;
+  double chol_level_ms[64] = {};
 };
 
 namespace sp {
@@ -227,6 +236,8 @@ struct LeafTask {
 void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 // X <- L^{-1} X (trans = false) or L^{-T} X (trans = true), L lower.
 void leaf_trsm(sp_ctx* ctx, bool trans, const std::vector<LeafTask>& tasks);
+// X <- L^{-1} (the whole n x n inverse) for lower-triangular leaves, n <= 1024.
+void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 
 // --------------------------------------------------------- recompression ----
 // A block given as a sum of products sum_s scale_s U_s V_s^T (U_s: m x w_s,

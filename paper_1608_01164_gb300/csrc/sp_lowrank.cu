@@ -8,8 +8,10 @@
 //   1. gather the stacked factors  W_U = [U_1 .. U_S]  (m x R) and
 //      W_V = [s_1 V_1 .. s_S V_S]  (q x R);
 //   2. Householder QR of W_U and W_V; tall factors use a binary TSQR tree of
-//      row chunks (every chunk and merge is one CTA), so a block of 50 000 rows
-//      spreads over many SMs;
+//      256-row chunks (every chunk and merge is one CTA), so a block of 50 000
+//      rows spreads over many SMs.  A merge stacks its children's R factors
+//      compactly: its row count and the children's row offsets follow from the
+//      actual width R on the device, so no stage works on padding;
 //   3. core  M = R_U R_V^T  (r_U x r_V, r = min(rows, R));
 //   4. one-sided (Hestenes) Jacobi SVD of M in one CTA, round-robin pair order;
 //   5. keep the k singular values > tol, U = Q_U [U~_k S_k; 0],
@@ -18,6 +20,7 @@
 // All sizes except the static upper bounds are device-resident (ranks produced
 // by earlier launches), so the whole pipeline is enqueued without a host sync.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 
@@ -79,15 +82,41 @@ __global__ void k_gather(const GatherBlock* __restrict__ blocks, const Seg* __re
   }
 }
 
+// Reads the device-resident widths the segments point at (one thread each).
+__global__ void k_read_widths(const int* const* __restrict__ p, int cnt, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) out[i] = *p[i];
+}
+
 // ---------------------------------------------------------- Householder QR --
+// Row counts of TSQR nodes.  A chunk has a static row count; a merge node
+// stacks the R factors of its children, min(rows_t, R) rows each, so its row
+// count (and every child's row offset in it) depends on the actual width R.
+struct RowRule {
+  int rows;         // chunk: its rows; merge: static capacity (R = Rmax)
+  int nkid;         // 0: chunk; > 0: merge of nkid children
+  int kid_rows[2];  // children's static row counts (merge)
+  int npre;         // earlier siblings in the parent (0 or 1)
+  int pre_rows;     // static row count of the earlier sibling
+};
+
+__device__ __forceinline__ int rule_rows(const RowRule& q, int R) {
+  if (q.nkid == 0) return q.rows;
+  int s = 0;
+  for (int t = 0; t < q.nkid; ++t) s += min(q.kid_rows[t], R);
+  return s;
+}
+
+__device__ __forceinline__ int rule_offset(const RowRule& q, int R) { return q.npre ? min(q.pre_rows, R) : 0; }
+
 // In-place QR of the rows x R matrix J (R = *pR <= Rmax).  Householder vectors
 // are stored below the diagonal with v_0 = 1 implicit, tau[j] their scalars.
-// The upper-trapezoidal factor is copied to dst (Rmax x Rmax slot, ld_dst),
-// zero elsewhere in the slot.
+// The upper-trapezoidal factor (nref x R, nref = min(rows, R), zeros below the
+// diagonal) is written at row offset rule_offset of dst (ld_dst).
 struct QrJob {
   double* J;
   int64_t ldj;
-  int rows;
+  RowRule rr;
   const int* pR;
   int Rmax;
   double* tau;
@@ -98,7 +127,7 @@ struct QrJob {
 __global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs, double* fc) {
   const QrJob jb = jobs[blockIdx.x];
   const int R = dwidth(jb.Rmax, jb.pR);
-  const int rows = jb.rows;
+  const int rows = rule_rows(jb.rr, R);
   double* J = jb.J;
   const int64_t ld = jb.ldj;
   const int nref = min(rows, R);
@@ -158,22 +187,23 @@ __global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs, doub
     for (int j = 0; j < nref; ++j) f += (double)(rows - j) * (2.0 + 4.0 * (R - j - 1));
     atomicAdd(fc, f);
   }
-  // copy R (nref x R upper trapezoid) into the Rmax x Rmax slot
-  for (int64_t e = threadIdx.x; e < (int64_t)jb.Rmax * jb.Rmax; e += blockDim.x) {
-    const int i = (int)(e % jb.Rmax), c = (int)(e / jb.Rmax);
-    double v = 0.0;
-    if (i < nref && c < R && i <= c) v = J[i + (int64_t)c * ld];
-    jb.dst[i + (int64_t)c * jb.ld_dst] = v;
+  // the R factor: nref x R upper trapezoid at its row offset in dst
+  double* dst = jb.dst + rule_offset(jb.rr, R);
+  for (int64_t e = threadIdx.x; e < (int64_t)nref * R; e += blockDim.x) {
+    const int i = (int)(e % nref), c = (int)(e / nref);
+    dst[i + (int64_t)c * jb.ld_dst] = (i <= c) ? J[i + (int64_t)c * ld] : 0.0;
   }
 }
 
 // out = Q [S; 0] where Q = H_0 H_1 ... H_{r-1} are the reflectors of a QrJob
-// (r = min(rows, R)); S: Rmax x k slot (rows beyond min(rows,R) ignored);
-// out: rows x cap, columns >= k set to zero.
+// (r = min(rows, R)); S: nref x k, read at row offset rule_offset(srule) of S
+// (the node's slot in its parent's output).  A chunk (final output) writes
+// rows x cap with columns >= k zero; a merge node writes only rows x k.
 struct ApplyJob {
   const double* J;
   int64_t ldj;
-  int rows;
+  RowRule rr;
+  RowRule srule;
   const int* pR;
   int Rmax;
   const double* tau;
@@ -188,16 +218,18 @@ struct ApplyJob {
 __global__ void __launch_bounds__(256) k_apply_q(const ApplyJob* __restrict__ jobs, double* fc) {
   const ApplyJob jb = jobs[blockIdx.x];
   const int R = dwidth(jb.Rmax, jb.pR);
-  const int rows = jb.rows;
+  const int rows = rule_rows(jb.rr, R);
   const int nref = min(rows, R);
   const int k = dwidth(jb.cap, jb.pk);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   double* O = jb.out;
   const int64_t ldo = jb.ldo;
-  for (int64_t e = threadIdx.x; e < (int64_t)rows * jb.cap; e += blockDim.x) {
+  const double* S = jb.S + rule_offset(jb.srule, R);
+  const int wcols = jb.rr.nkid == 0 ? jb.cap : k;
+  for (int64_t e = threadIdx.x; e < (int64_t)rows * wcols; e += blockDim.x) {
     const int i = (int)(e % rows), c = (int)(e / rows);
     double v = 0.0;
-    if (c < k && i < nref) v = jb.S[i + (int64_t)c * jb.lds];
+    if (c < k && i < nref) v = S[i + (int64_t)c * jb.lds];
     O[i + (int64_t)c * ldo] = v;
   }
   __syncthreads();
@@ -529,10 +561,10 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
   }
   __syncthreads();
   const int k = s_k;
-  // S_U = Q1 [B(:, perm2) ; 0]  (ru rows, k columns)
-  for (int64_t e = threadIdx.x; e < (int64_t)ld * jb.cap; e += blockDim.x) {
-    const int r = (int)(e % ld), p = (int)(e / ld);
-    jb.SU[r + (int64_t)p * ld] = (p < k && r < rp) ? B[r + (int64_t)perm2[p] * ld] : 0.0;
+  // S_U = Q1 [B(:, perm2) ; 0]  (ru rows, k columns; the applies read no more)
+  for (int64_t e = threadIdx.x; e < (int64_t)ru * k; e += blockDim.x) {
+    const int r = (int)(e % ru), p = (int)(e / ru);
+    jb.SU[r + (int64_t)p * ld] = (r < rp) ? B[r + (int64_t)perm2[p] * ld] : 0.0;
   }
   __syncthreads();
   for (int j = rp - 1; j >= 0; --j) {
@@ -549,10 +581,6 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
   for (int j = rp - 1; j >= 0; --j) {
     apply_reflector(A2, ld, j, rv, tau2[j], W, ld, 0, k, nullptr);
     __syncthreads();
-  }
-  for (int64_t e = threadIdx.x; e < (int64_t)ld * jb.cap; e += blockDim.x) {
-    const int r = (int)(e % ld), p = (int)(e / ld);
-    if (p >= k || r >= rv) jb.SV[r + (int64_t)p * ld] = 0.0;
   }
   for (int64_t e = threadIdx.x; e < (int64_t)rv * k; e += blockDim.x) {
     const int r = (int)(e % rv), p = (int)(e / rv);
@@ -575,31 +603,34 @@ struct TreePlan {
 }  // namespace
 
 // Builds the TSQR tree of one side (rows x Rmax matrix W, device width pR),
-// leaving the final R factor in `rdst` (Rmax x Rmax, ld Rmax) and arranging
-// for Q [S; 0] to be written into `out` (rows x cap, ld ldo).
-static void plan_side(double* W, int64_t ldw, int rows, const int* pR, int Rmax, double* rdst, const double* S,
-                      const int* pk, int cap, double* out, int64_t ldo, std::vector<std::vector<QrJob>>& qrl,
-                      std::vector<std::vector<ApplyJob>>& apl, std::vector<DBuf>& keep, cudaStream_t st) {
-  const int CH = std::max(256, ((4 * Rmax + 31) / 32) * 32);
+// leaving the final R factor in `rdst` (ld ldr) and arranging for Q [S; 0]
+// (S with ld ldr) to be written into `out` (rows x cap, ld ldo).  Each merge
+// stacks two children's R factors (at most min(rows_t, Rmax) rows each).
+static void plan_side(double* W, int64_t ldw, int rows, const int* pR, int Rmax, double* rdst, int64_t ldr,
+                      const double* S, const int* pk, int cap, double* out, int64_t ldo,
+                      std::vector<std::vector<QrJob>>& qrl, std::vector<std::vector<ApplyJob>>& apl,
+                      std::vector<DBuf>& keep, cudaStream_t st) {
+  // chunks of at least 2 Rmax rows, so that a merge (<= 2 Rmax rows) is never
+  // taller than a chunk
+  const int kChunk = std::max(256, (2 * Rmax + 31) / 32 * 32);
   struct Node {
     double* J;
     int64_t ldj;
-    int rows;
+    RowRule rr;
     double* tau;
-    int parent;       // index into nodes, -1 for root
-    int slot;         // row slot in the parent's matrix
-    int64_t out_row;  // for leaves: row offset in `out`
-    double* app_out;  // apply output buffer (internal: own temp, leaf: out + row)
+    int parent;       // index into the next level, -1 for the root
+    int slot;         // 0 or 1 within the parent
+    double* app_out;  // apply output (merge: own buffer, chunk: out + row)
     int64_t ldapp;
   };
+  auto chunk_rule = [](int r) { return RowRule{r, 0, {0, 0}, 0, 0}; };
   std::vector<std::vector<Node>> lv;
-  // level 0: chunks
   std::vector<Node> l0;
-  const int nch = rows <= CH ? 1 : (rows + CH - 1) / CH;
+  const int nch = rows <= kChunk ? 1 : (rows + kChunk - 1) / kChunk;
   for (int c = 0; c < nch; ++c) {
-    const int r0 = c * CH;
-    const int rr = std::min(CH, rows - r0);
-    l0.push_back(Node{W + r0, ldw, rr, nullptr, -1, 0, r0, out + r0, ldo});
+    const int r0 = c * kChunk;
+    const int rr = std::min(kChunk, rows - r0);
+    l0.push_back(Node{W + r0, ldw, chunk_rule(rr), nullptr, -1, 0, out + r0, ldo});
   }
   lv.push_back(l0);
   while (lv.back().size() > 1) {
@@ -607,13 +638,21 @@ static void plan_side(double* W, int64_t ldw, int rows, const int* pR, int Rmax,
     std::vector<Node> nxt;
     for (size_t i = 0; i < cur.size(); i += 2) {
       const int nchild = (i + 1 < cur.size()) ? 2 : 1;
-      const int mrows = nchild * Rmax;
-      keep.emplace_back((size_t)mrows * Rmax * sizeof(double), st);
+      RowRule m{0, nchild, {0, 0}, 0, 0};
+      for (int t = 0; t < nchild; ++t) {
+        m.kid_rows[t] = cur[i + t].rr.rows;
+        m.rows += std::min(cur[i + t].rr.rows, Rmax);
+      }
+      keep.emplace_back((size_t)m.rows * Rmax * sizeof(double) + 16, st);
       double* Mb = keep.back().as<double>();
-      nxt.push_back(Node{Mb, mrows, mrows, nullptr, -1, 0, 0, nullptr, 0});
+      nxt.push_back(Node{Mb, m.rows, m, nullptr, -1, 0, nullptr, 0});
       for (int t = 0; t < nchild; ++t) {
         cur[i + t].parent = (int)nxt.size() - 1;
         cur[i + t].slot = t;
+        if (t == 1) {
+          cur[i + t].rr.npre = 1;
+          cur[i + t].rr.pre_rows = cur[i].rr.rows;
+        }
       }
     }
     lv.push_back(nxt);
@@ -626,38 +665,24 @@ static void plan_side(double* W, int64_t ldw, int rows, const int* pR, int Rmax,
       keep.emplace_back((size_t)Rmax * sizeof(double) + 16, st);
       nd.tau = keep.back().as<double>();
       if (l > 0) {
-        keep.emplace_back((size_t)nd.rows * cap * sizeof(double) + 16, st);
+        keep.emplace_back((size_t)nd.rr.rows * cap * sizeof(double) + 16, st);
         nd.app_out = keep.back().as<double>();
-        nd.ldapp = nd.rows;
+        nd.ldapp = nd.rr.rows;
       }
     }
   }
-  for (size_t l = 0; l < lv.size(); ++l) {
+  const size_t depth = lv.size();
+  for (size_t l = 0; l < depth; ++l) {
     for (auto& nd : lv[l]) {
-      double* dst;
-      int64_t ldd;
-      if (l + 1 < lv.size()) {
-        Node& par = lv[l + 1][nd.parent];
-        dst = par.J + (int64_t)nd.slot * Rmax;
-        ldd = par.ldj;
-      } else {
-        dst = rdst;
-        ldd = Rmax;
-      }
-      qrl[l].push_back(QrJob{nd.J, nd.ldj, nd.rows, pR, Rmax, nd.tau, dst, ldd});
-      const double* Sin;
-      int64_t lds;
-      if (l + 1 < lv.size()) {
-        Node& par = lv[l + 1][nd.parent];
-        Sin = par.app_out + (int64_t)nd.slot * Rmax;
-        lds = par.ldapp;
-      } else {
-        Sin = S;
-        lds = Rmax;
-      }
-      // apply levels are run from the top: store at index (depth-1-l)
-      const size_t depth = lv.size();
-      apl[depth - 1 - l].push_back(ApplyJob{nd.J, nd.ldj, nd.rows, pR, Rmax, nd.tau, Sin, lds, nd.app_out,
+      const bool root = (l + 1 == depth);
+      double* dst = root ? rdst : lv[l + 1][nd.parent].J;
+      const int64_t ldd = root ? ldr : lv[l + 1][nd.parent].ldj;
+      // the node's own row rule carries its offset in the parent (npre/pre_rows)
+      qrl[l].push_back(QrJob{nd.J, nd.ldj, nd.rr, pR, Rmax, nd.tau, dst, ldd});
+      const double* Sin = root ? S : lv[l + 1][nd.parent].app_out;
+      const int64_t lds = root ? ldr : lv[l + 1][nd.parent].ldapp;
+      // apply levels run from the top: store at index (depth-1-l)
+      apl[depth - 1 - l].push_back(ApplyJob{nd.J, nd.ldj, nd.rr, nd.rr, pR, Rmax, nd.tau, Sin, lds, nd.app_out,
                                             nd.ldapp, pk, cap});
     }
   }
@@ -669,23 +694,49 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
   const int nb = (int)blocks.size();
   std::vector<Seg> segs;
   std::vector<GatherBlock> gb(nb);
-  std::vector<int> Rmax(nb);
+  std::vector<int> Rmax(nb), Rs(nb);
+  // Exact stacked widths: the segments' widths live on the device (ranks
+  // produced by earlier launches); read them once so that every buffer, chunk
+  // and slot below is sized by the actual width instead of the capacities.
+  std::vector<const int*> wptr;
+  for (const LrBlock& b : blocks)
+    for (const Seg& sg : b.segs)
+      if (sg.pw) wptr.push_back(sg.pw);
+  std::vector<int> wval(wptr.size());
+  if (!wptr.empty()) {
+    DBuf dp = upload(wptr, st);
+    DBuf dv(wptr.size() * sizeof(int) + 16, st);
+    k_read_widths<<<(unsigned)((wptr.size() + 255) / 256), 256, 0, st>>>(dp.as<const int*>(), (int)wptr.size(),
+                                                                           dv.as<int>());
+    check_launch("k_read_widths");
+    check_cuda(cudaMemcpyAsync(wval.data(), dv.p, wval.size() * sizeof(int), cudaMemcpyDeviceToHost, st), "widths");
+    const auto t0 = std::chrono::steady_clock::now();
+    check_cuda(cudaStreamSynchronize(st), "sync");
+    if (ctx->profiling) {
+      ctx->ms[KID_HOST_WAIT] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      ctx->launches[KID_HOST_WAIT] += 1;
+    }
+  }
   size_t wsz = 0, csz = 0;
   int maxseg = 1, maxrows = 1, maxR = 1;
+  size_t wi = 0;
   for (int t = 0; t < nb; ++t) {
     const LrBlock& b = blocks[t];
     int R = 0;
-    for (const Seg& s : b.segs) R += s.w;
+    for (const Seg& sg : b.segs) {
+      int w = sg.w;
+      if (sg.pw) w = std::min(sg.w, std::max(wval[wi++], 0));
+      R += w;
+    }
     Rmax[t] = std::max(R, 1);
+    // R factors, core and SVD work have at most min(max(m, q), R) rows
+    Rs[t] = std::max(1, std::min(std::max(b.m, b.q), Rmax[t]));
     wsz += (size_t)(b.m + b.q) * Rmax[t];
-    csz += (size_t)Rmax[t] * Rmax[t] * 3 + 2 * (size_t)Rmax[t] * b.cap;
+    csz += 2 * (size_t)Rs[t] * Rmax[t] + (size_t)Rs[t] * Rs[t] + 2 * (size_t)Rs[t] * b.cap;
     maxseg = std::max(maxseg, (int)b.segs.size());
     maxrows = std::max(maxrows, std::max(b.m, b.q));
-    maxR = std::max(maxR, Rmax[t]);
-    for (const Seg& s : b.segs) {
-      ctx->flops += 4.0 * (double)(b.m + b.q) * Rmax[t] * Rmax[t];
-      (void)s;
-    }
+    maxR = std::max(maxR, Rs[t]);
+    ctx->flops += 4.0 * (double)(b.m + b.q) * Rmax[t] * Rmax[t];
   }
   std::vector<DBuf> keep;
   DBuf wbuf(wsz * sizeof(double) + 64, st);
@@ -721,23 +772,24 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     g.R = ip + 4 * t;
     g.ru = ip + 4 * t + 1;
     g.rv = ip + 4 * t + 2;
-    double* RU = cp;
-    cp += (size_t)Rm * Rm;
+    const int Rr = Rs[t];
+    double* RU = cp;  // Rr x Rm, ld Rr
+    cp += (size_t)Rr * Rm;
     double* RV = cp;
-    cp += (size_t)Rm * Rm;
-    double* M = cp;
-    cp += (size_t)Rm * Rm;
-    double* SU = cp;
-    cp += (size_t)Rm * b.cap;
+    cp += (size_t)Rr * Rm;
+    double* M = cp;  // Rr x Rr
+    cp += (size_t)Rr * Rr;
+    double* SU = cp;  // Rr x cap
+    cp += (size_t)Rr * b.cap;
     double* SV = cp;
-    cp += (size_t)Rm * b.cap;
-    plan_side(g.WU, b.m, b.m, g.R, Rm, RU, SU, b.rank_out, b.cap, b.Uout, b.ldu_out, qrl, apl, keep, st);
-    plan_side(g.WV, b.q, b.q, g.R, Rm, RV, SV, b.rank_out, b.cap, b.Vout, b.ldv_out, qrl, apl, keep, st);
+    cp += (size_t)Rr * b.cap;
+    plan_side(g.WU, b.m, b.m, g.R, Rm, RU, Rr, SU, b.rank_out, b.cap, b.Uout, b.ldu_out, qrl, apl, keep, st);
+    plan_side(g.WV, b.q, b.q, g.R, Rm, RV, Rr, SV, b.rank_out, b.cap, b.Vout, b.ldv_out, qrl, apl, keep, st);
     // M = R_U R_V^T (ru x rv, inner dimension R)
-    core.push_back(gt(RU, Rm, RV, Rm, M, Rm, Rm, Rm, Rm, 1.0, 0.0, g.ru, g.rv, g.R));
-    keep.emplace_back((size_t)Rm * Rm * 3 * sizeof(double) + 16, st);
+    core.push_back(gt(RU, Rr, RV, Rr, M, Rr, Rr, Rr, Rm, 1.0, 0.0, g.ru, g.rv, g.R));
+    keep.emplace_back((size_t)Rr * Rr * 3 * sizeof(double) + 16, st);
     double* Gw = keep.back().as<double>();
-    svd[t] = SvdJob{M, g.ru, g.rv, Rm, Gw, Gw + (size_t)Rm * Rm, Gw + 2 * (size_t)Rm * Rm, SU, SV, b.rank_out, b.cap};
+    svd[t] = SvdJob{M, g.ru, g.rv, Rr, Gw, Gw + (size_t)Rr * Rr, Gw + 2 * (size_t)Rr * Rr, SU, SV, b.rank_out, b.cap};
   }
   // 1. gather
   {
@@ -769,8 +821,8 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     if (sm > 48 * 1024)
       check_cuda(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
                  "smem attr");
-    ProfScope ps(ctx, KID_JACOBI);
-    k_core_svd<<<(unsigned)nb, 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags, fc_ptr(ctx, KID_JACOBI));
+    ProfScope ps(ctx, KID_CORE_SVD);
+    k_core_svd<<<(unsigned)nb, 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags, fc_ptr(ctx, KID_CORE_SVD));
     check_launch("k_core_svd");
   }
   // 5. apply reflectors top-down

@@ -21,6 +21,10 @@
 namespace sp {
 namespace {
 
+// widest band handled by the warp-per-shift count (4 windows of (b+1)^2 doubles
+// per 128-thread CTA must fit in shared memory)
+constexpr int kWarpInertiaMaxB = 80;
+
 __global__ void k_inertia(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
                           const double* __restrict__ shifts, int nshift, int64_t* __restrict__ counts, double pivmin,
                           double* __restrict__ ring) {
@@ -63,6 +67,70 @@ __global__ void k_inertia(const double* __restrict__ ab, int64_t ldab, int64_t n
     }
   }
   counts[t] = cnt;
+}
+
+// Banded LDL^T count with one warp per shift (b >= 2).  The trailing
+// (b+1) x (b+1) window of the Schur complement of A - sigma I is kept, both
+// triangles, in shared memory as a ring over row/column indices (global index
+// r lives in slot r mod (b+1)).  Step j: pivot d_j = S(j, j); every lane
+// updates its share of the b^2 entries S(r, c) -= S(r, j) S(c, j) / d_j,
+// r, c in (j, j+b]; then row/column j+b+1 of A enters the slot of j.  Same
+// arithmetic as the per-thread ring above, summed in a different order.
+__global__ void __launch_bounds__(128) k_inertia_warp(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+                                                      const double* __restrict__ shifts, int nshift,
+                                                      int64_t* __restrict__ counts, double pivmin) {
+  extern __shared__ double win_all[];
+  const int W = b + 1;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int t = blockIdx.x * (blockDim.x >> 5) + wib;
+  if (t >= nshift) return;  // whole warps exit together
+  double* S = win_all + (size_t)wib * W * W;
+  const double sigma = shifts[t];
+  // window rows/columns 0..b
+  for (int e = lane; e < W * W; e += 32) {
+    const int r = e / W, c = e % W;
+    double v = 0.0;
+    if (r < n && c < n) {
+      const int hi = r > c ? r : c, lo = r > c ? c : r;
+      if (hi - lo <= b) v = ab[(hi - lo) + (int64_t)lo * ldab];
+      if (r == c) v -= sigma;
+    }
+    S[e] = v;
+  }
+  __syncwarp();
+  int64_t cnt = 0;
+  int sj = 0;  // slot of row j
+  for (int64_t j = 0; j < n; ++j) {
+    double d = S[sj * W + sj];
+    if (fabs(d) < pivmin) d = -pivmin;
+    cnt += d < 0.0;
+    const double inv = 1.0 / d;
+    const int lim = (int)((n - 1 - j) < b ? (n - 1 - j) : b);  // rows j+1..j+lim exist
+    for (int e = lane; e < lim * lim; e += 32) {
+      const int ro = e / lim + 1, co = e % lim + 1;
+      int sr = sj + ro, sc = sj + co;
+      if (sr >= W) sr -= W;
+      if (sc >= W) sc -= W;
+      S[sr * W + sc] -= S[sr * W + sj] * S[sc * W + sj] * inv;
+    }
+    __syncwarp();
+    // row/column j+b+1 of A - sigma I into slot sj
+    const int64_t r = j + b + 1;
+    if (r < n) {
+      for (int co = lane; co <= b; co += 32) {
+        const int64_t c = j + 1 + co;  // c in [j+1, r]
+        double v = ab[(r - c) + c * ldab];
+        if (c == r) v -= sigma;
+        int sc = sj + 1 + co;
+        if (sc >= W) sc -= W;
+        S[sj * W + sc] = v;
+        S[sc * W + sj] = v;
+      }
+    }
+    __syncwarp();
+    sj = (sj + 1 == W) ? 0 : sj + 1;
+  }
+  if (lane == 0) counts[t] = cnt;
 }
 
 __global__ void k_gershgorin(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, double* out) {
@@ -204,6 +272,17 @@ void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t
   double amax = 1.0;
   for (double v : h) amax = std::max(amax, v);
   const double pivmin = DBL_MIN * amax * amax;
+  if (b >= 2 && b <= kWarpInertiaMaxB) {
+    const size_t sm = (size_t)4 * (b + 1) * (b + 1) * sizeof(double);
+    if (sm > 48 * 1024)
+      check_cuda(cudaFuncSetAttribute(k_inertia_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                 "smem attr");
+    ProfScope ps(ctx, KID_INERTIA);
+    k_inertia_warp<<<(nshift + 3) / 4, 128, sm, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev,
+                                                               pivmin);
+    check_launch("k_inertia_warp");
+    return;
+  }
   DBuf ring(b > 1 ? (size_t)nshift * (b * b + b) * sizeof(double) : 16, ctx->stream);
   ProfScope ps(ctx, KID_INERTIA);
   k_inertia<<<(nshift + 63) / 64, 64, 0, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev, pivmin,

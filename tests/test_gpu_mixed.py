@@ -68,3 +68,41 @@ def test_mixed_precision_error_before_and_after_polish(ctx, name, n, b, leaf):
     assert e0 <= 1e-5                                   # before the polish: binary32-level at worst
     assert round(tr64) == nu and round(trm1) == nu
     print(f"{name}: FP64 {e64:.2e}  mixed before polish {e0:.2e}  after polish {e1:.2e}")
+
+
+@pytest.mark.parametrize("name,n,b,leaf", [("band16", 1024, 16, 64), ("tridiag", 1024, 1, 64)])
+def test_mixed_newton_schulz_tail(ctx, name, n, b, leaf):
+    """Late QDWH steps replaced by residual-form Newton-Schulz steps (binary32
+    products): same bar against the binary64 oracle."""
+    if b == 16:
+        ab = sp_inputs.normal_band(n, 16, seed=2024, scale=1.0 / math.sqrt(16.0))
+    else:
+        (_, ab, _), = sp_inputs.workload(0, n=n)
+    nu = n // 2
+    sh = oracle.locate_mu(ab, nu)
+    Pref, _, _ = oracle.projector(ab, sh.mu)
+    Pn, trn, inn = projector(ctx, ab, sh.mu, leaf, sp.SP_MIXED_NS, 1)
+    kinds = list(inn.kind[:inn.iters])
+    assert kinds[0] == 1 and 4 in kinds and 3 not in kinds, kinds
+    # the tail starts where 1 - l_k^2 <= 1e-2; every step before it is a Cholesky step
+    first_ns = kinds.index(4)
+    assert all(k == 2 for k in kinds[1:first_ns])
+    assert all(k == 4 for k in kinds[first_ns:])
+    assert 1.0 - inn.l[first_ns] ** 2 <= 1e-2
+    e = oracle.sym_norm2(Pn - Pref)
+    assert e <= 1e-8, e
+    assert round(trn) == nu
+    print(f"{name}: mixed Newton-Schulz tail {kinds} error {e:.2e}")
+
+
+def test_mixed_rejects_bad_precision(ctx):
+    ab = sp_inputs.uniform_band(64, 1, 3)
+    A = sp.sp_hodlr_from_band(ctx, ab, 0.0, 16, 1e-10)
+    try:
+        o = sp.sp_qdwh_opts_default()
+        o.precision = 7
+        with pytest.raises(sp.SpError) as ei:
+            sp.sp_qdwh_sign(ctx, A, o)
+        assert ei.value.code == sp.SP_EINVAL
+    finally:
+        sp.sp_hodlr_destroy(A)

@@ -166,7 +166,7 @@ def test_fastqr_factors_match_replay(ctx, keep, n, b, leaf):
 
 # ------------------------------------------------- parameter estimation ----
 
-@pytest.mark.parametrize("n,b", [(500, 1), (400, 4)])
+@pytest.mark.parametrize("n,b", [(500, 1), (400, 4), (700, 16), (300, 33), (200, 90)])
 def test_inertia_counts(ctx, n, b):
     ab = sp_inputs.normal_band(n, b, seed=51)
     w = np.linalg.eigvalsh(sp_inputs.dense_from_band(ab))
