@@ -339,6 +339,8 @@ def run_ours(args):
             "detail": {"iters": info.iters, "kinds": list(info.kind[:info.iters]), "max_rank": info.max_rank,
                        "alpha": info.alpha, "l0": info.l0, "ms_polish": info.ms_polish,
                        "ms_param": info.ms_param, "ms_qr": info.ms_qr, "ms_chol": info.ms_chol,
+                       "ms_chol_phases": {"square": info.ms_mult, "factor": info.ms_factor, "solve": info.ms_solve,
+                                          "combine": info.ms_combine},
                        "trace_minus_nu": traces[-1] - nu, "wall_s": t_wall,
                        "chol_self_ms_per_level": chol_levels,
                        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "gflop": round(v[2] / 1e9, 3)}

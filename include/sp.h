@@ -173,7 +173,10 @@ int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out);
 
 /* Y = M X for a HODLR M and a dense n x nrhs block X (HODLR matrix-vector
  * product, Table "complexity_HODLR": O(k n log n) per column).
- * X, Y: device pointers, column-major, ldx, ldy >= n; Y must not alias X. */
+ * X, Y: column-major, ldx, ldy >= n; Y must not alias X.  Device pointers:
+ * the product is enqueued on the context's stream (asynchronous).  Host
+ * pointers (either one): the operand is staged through device memory and the
+ * call returns once Y holds the result. */
 int sp_apply(sp_ctx_t ctx, sp_hodlr_t M, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy);
 
 /* Rows row0 .. row0+nrows-1 of M as a dense nrows x n panel (column-major,

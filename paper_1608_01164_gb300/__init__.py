@@ -78,7 +78,7 @@ def build(force: bool = False, jobs: int = 6) -> str:
     with ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(compile_one, srcs))
     tmp = LIB_PATH + f".tmp{os.getpid()}"
-    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs])
+    subprocess.check_call(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-Xlinker", "--no-undefined", "-o", tmp, *objs])
     os.replace(tmp, LIB_PATH)
     return LIB_PATH
 

@@ -299,6 +299,17 @@ int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
     check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
     check_cuda(cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS), "flags");
     check_cuda(cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS), "flags");
+    {
+      static std::mutex mu;
+      static bool configured[64] = {};
+      std::lock_guard<std::mutex> lock(mu);
+      if (ctx->device >= 0 && ctx->device < 64 && !configured[ctx->device]) {
+        configure_blas_kernels();
+        configure_lowrank_kernels();
+        configure_param_kernels();
+        configured[ctx->device] = true;
+      }
+    }
     // Every formatted operation allocates and frees its temporaries in stream
     // order from the device's default pool.  Keep freed memory in the pool
     // across synchronisations (the default threshold 0 hands it back to the
@@ -647,9 +658,36 @@ int sp_apply(sp_ctx_t ctx, sp_hodlr_t M, int64_t nrhs, const double* X, int64_t 
   if (!ctx || !M || !X || !Y || nrhs < 0 || ldx < M->n() || ldy < M->n()) return SP_EINVAL;
   if (nrhs == 0) return SP_OK;
   return guarded(ctx, [&] {
+    const int64_t n = M->n();
+    const bool hx = !is_device(X), hy = !is_device(Y);
+    // host operands are staged through device buffers and the call returns
+    // once Y holds the result; device operands stay asynchronous
+    DBuf dx(hx ? (size_t)n * nrhs * sizeof(double) : 0, ctx->stream);
+    DBuf dy(hy ? (size_t)n * nrhs * sizeof(double) : 0, ctx->stream);
+    const double* Xd = X;
+    int64_t ldxd = ldx;
+    double* Yd = Y;
+    int64_t ldyd = ldy;
+    if (hx) {
+      check_cuda(cudaMemcpy2DAsync(dx.p, n * sizeof(double), X, ldx * sizeof(double), n * sizeof(double), nrhs,
+                                   cudaMemcpyHostToDevice, ctx->stream),
+                 "apply X upload");
+      Xd = dx.as<double>();
+      ldxd = n;
+    }
+    if (hy) {
+      Yd = dy.as<double>();
+      ldyd = n;
+    }
     for (int64_t c0 = 0; c0 < nrhs; c0 += 256) {
       const int w = (int)std::min<int64_t>(256, nrhs - c0);
-      hodlr_apply_level(ctx, M, 0, X + c0 * ldx, ldx, Y + c0 * ldy, ldy, w, nullptr, false, false);
+      hodlr_apply_level(ctx, M, 0, Xd + c0 * ldxd, ldxd, Yd + c0 * ldyd, ldyd, w, nullptr, false, false);
+    }
+    if (hy) {
+      check_cuda(cudaMemcpy2DAsync(Y, ldy * sizeof(double), Yd, n * sizeof(double), n * sizeof(double), nrhs,
+                                   cudaMemcpyDeviceToHost, ctx->stream),
+                 "apply Y download");
+      check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
     }
   });
 }

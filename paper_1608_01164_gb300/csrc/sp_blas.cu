@@ -8,6 +8,8 @@
 // FP64 pipe (ridge ~0.18 flop/byte); the tiling aims at keeping each SM's
 // DFMA pipe busy, not at saving bytes.
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <atomic>
 #include <cstdio>
 #include <stdexcept>
@@ -69,6 +71,26 @@ void dfree(void* p, cudaStream_t st) {
 
 DBuf::DBuf(size_t b, cudaStream_t s) : p(dmalloc(b, s)), bytes(b), st(s) {}
 DBuf::~DBuf() { dfree(p, st); }
+
+void configure_dynamic_smem(const void* func) {
+  int dev = 0, optin = 0;
+  check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+  check_cuda(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev), "smem opt-in");
+  cudaFuncAttributes fa;
+  check_cuda(cudaFuncGetAttributes(&fa, func), "function attributes");
+  const int dyn = optin - (int)fa.sharedSizeBytes;
+  if (dyn > fa.maxDynamicSharedSizeBytes)
+    check_cuda(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn), "smem attribute");
+}
+
+void ensure_dynamic_smem(const void* func, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  cudaFuncAttributes fa;
+  check_cuda(cudaFuncGetAttributes(&fa, func), "function attributes");
+  if (bytes > (size_t)fa.maxDynamicSharedSizeBytes)
+    fail(SP_EINVAL, "problem needs " + std::to_string(bytes) + " bytes of shared memory per CTA, above the limit " +
+                        std::to_string(fa.maxDynamicSharedSizeBytes));
+}
 
 // ------------------------------------------------------------ batched GEMM --
 namespace {
@@ -206,7 +228,8 @@ __global__ void k_zero_tail(const ZeroTailTask* __restrict__ tasks) {
 }
 
 // Blocked right-looking Cholesky of one leaf per CTA (1024 threads): each
-// 32-column panel (rows jb..n-1) is factored in shared memory, written back,
+// 32-column panel (rows jb..n-1) is factored in shared memory (two barriers
+// per column, pivots by one thread), written back,
 // and the trailing lower triangle gets A22 -= P P^T, every thread producing
 // 2x2 outputs from the shared-memory panel.  The upper triangle is zeroed.
 constexpr int kPW = 32;  // panel width
@@ -219,6 +242,8 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* P = reinterpret_cast<double*>(smem_raw);  // panel, row-major (n rows x (kPW+1))
   constexpr int LDP = kPW + 1;
+  __shared__ double dsq[kPW];
+  __shared__ double s_inv;
   for (int jb = 0; jb < n; jb += kPW) {
     const int w = min(kPW, n - jb);
     const int pr = n - jb;  // panel rows
@@ -227,27 +252,38 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
       P[r * LDP + c] = A[(jb + r) + (int64_t)(jb + c) * lda];
     }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-      if (threadIdx.x == 0) {
-        double d = P[j * LDP + j];
-        if (!(d > 0.0)) {
-          atomicOr(&flags[FLAG_BREAKDOWN], 1);
-          d = 1.0;
-        }
-        P[j * LDP + j] = sqrt(d);
+    // Square roots and reciprocals of the pivots are taken by thread 0 only:
+    // binary64 divides and square roots are expensive on this part, and 1024
+    // threads repeating them would cost more than the factorisation.  Thread
+    // 0 also updates the next pivot (its first element of every update phase),
+    // so the next reciprocal is ready at the barrier that ends the phase.
+    auto pivot = [&](int j) {
+      double d = P[j * LDP + j];
+      if (!(d > 0.0)) {
+        atomicOr(&flags[FLAG_BREAKDOWN], 1);
+        d = 1.0;
       }
-      __syncthreads();
-      const double inv = 1.0 / P[j * LDP + j];
+      d = sqrt(d);
+      dsq[j] = d;
+      s_inv = 1.0 / d;
+    };
+    if (threadIdx.x == 0) pivot(0);
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+      const double inv = s_inv;
       for (int r = j + 1 + threadIdx.x; r < pr; r += blockDim.x) P[r * LDP + j] *= inv;
       __syncthreads();
-      // update panel columns j+1..w-1, rows >= column
+      // update panel columns j+1..w-1, rows >= column (element 0 is the next pivot)
       const int nc = w - j - 1;
       for (int e = threadIdx.x; e < (pr - j - 1) * nc; e += blockDim.x) {
         const int r = j + 1 + e / nc, c = j + 1 + e % nc;
         if (r >= c) P[r * LDP + c] -= P[r * LDP + j] * P[c * LDP + j];
       }
+      if (threadIdx.x == 0 && j + 1 < w) pivot(j + 1);
       __syncthreads();
     }
+    if (threadIdx.x < w) P[threadIdx.x * LDP + threadIdx.x] = dsq[threadIdx.x];
+    __syncthreads();
     for (int e = threadIdx.x; e < pr * w; e += blockDim.x) {
       const int r = e % pr, c = e / pr;
       A[(jb + r) + (int64_t)(jb + c) * lda] = (r >= c) ? P[r * LDP + c] : 0.0;
@@ -395,6 +431,64 @@ __global__ void __launch_bounds__(256) k_leaf_inv(const LeafTask* __restrict__ t
         if (c0 + c < n) t.X[i + (int64_t)(c0 + c) * t.ldx] = x[r][c];
   }
 }
+
+// Same forward substitution as k_leaf_inv, with the part of L the block needs
+// (columns c0..n-1, lower triangle) staged once in shared memory, packed by
+// columns, so a step costs a shared-memory read and one barrier instead of a
+// round trip to L2.  For leaves of at most kInvSmemRows rows.
+constexpr int kInvSmemRows = 220;
+
+__global__ void __launch_bounds__(256) k_leaf_inv_smem(const LeafTask* __restrict__ tasks) {
+  const LeafTask t = tasks[blockIdx.y];
+  const int n = t.n;
+  const int c0 = blockIdx.x * kInvCols;
+  if (c0 >= n) return;
+  const double* L = t.A;
+  const int64_t lda = t.lda;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double* Ls = reinterpret_cast<double*>(smem_raw);  // packed columns c0..n-1
+  __shared__ double dinv[kInvSmemRows];
+  __shared__ double piv[2][kInvCols];
+  const int m = n - c0;
+  // column j (j >= c0) holds rows j..n-1 at offset off(j) = sum_{t<j-c0} (m - t)
+  for (int jj = threadIdx.x >> 5; jj < m; jj += blockDim.x >> 5) {
+    const int64_t off = (int64_t)jj * m - (int64_t)jj * (jj - 1) / 2;
+    const int j = c0 + jj;
+    for (int i = j + (threadIdx.x & 31); i < n; i += 32) Ls[off + (i - j)] = L[i + (int64_t)j * lda];
+  }
+  __syncthreads();
+  for (int jj = threadIdx.x; jj < m; jj += blockDim.x) {
+    const int64_t off = (int64_t)jj * m - (int64_t)jj * (jj - 1) / 2;
+    dinv[jj] = 1.0 / Ls[off];
+  }
+  const int i = threadIdx.x;  // one row per thread (n <= 220 < 256)
+  double x[kInvCols];
+#pragma unroll
+  for (int c = 0; c < kInvCols; ++c) x[c] = (i == c0 + c) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int j = c0; j < n; ++j) {
+    const int jj = j - c0;
+    if (i == j) {
+      const double di = dinv[jj];
+#pragma unroll
+      for (int c = 0; c < kInvCols; ++c) {
+        x[c] *= di;
+        piv[j & 1][c] = x[c];
+      }
+    }
+    __syncthreads();
+    if (i > j && i < n) {
+      const int64_t off = (int64_t)jj * m - (int64_t)jj * (jj - 1) / 2;
+      const double l = Ls[off + (i - j)];
+#pragma unroll
+      for (int c = 0; c < kInvCols; ++c) x[c] = fma(-l, piv[j & 1][c], x[c]);
+    }
+  }
+  if (i < n)
+#pragma unroll
+    for (int c = 0; c < kInvCols; ++c)
+      if (c0 + c < n) t.X[i + (int64_t)(c0 + c) * t.ldx] = x[c];
+}
 }  // namespace
 
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, bool atomic, int ksplit) {
@@ -413,8 +507,11 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
   int nz = 1, kchunk = std::max(maxk, 1);
   if (ksplit <= 0) {
     const int64_t ctas = (int64_t)maxtiles * (int64_t)tasks.size();
-    if (maxk >= 1024 && ctas < 2 * ctx->num_sms) {
-      nz = (int)std::min<int64_t>((4 * ctx->num_sms + ctas - 1) / ctas, maxk / 256);
+    // binary64 runs at about 8 GFLOP/s per SM on this part, so a GEMM spread
+    // over a few CTAs is compute-bound on a few SMs: split k (chunks of at
+    // least 64) until the grid covers the GPU
+    if (maxk >= 128 && ctas < 2 * ctx->num_sms) {
+      nz = (int)std::min<int64_t>((4 * ctx->num_sms + ctas - 1) / ctas, maxk / 64);
       nz = std::max(nz, 1);
     }
   } else {
@@ -490,8 +587,7 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   int nmax = 1;
   for (const auto& t : tasks) nmax = std::max(nmax, t.n);
   const size_t sm = (size_t)nmax * (kPW + 1) * sizeof(double);
-  if (sm > 48 * 1024)
-    check_cuda(cudaFuncSetAttribute(k_leaf_potrf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm), "smem");
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf), sm);
   ProfScope ps(ctx, KID_POTRF);
   k_leaf_potrf<<<(unsigned)tasks.size(), 1024, sm, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags);
   check_launch("k_leaf_potrf");
@@ -523,15 +619,28 @@ void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
     if (t.n > kInvRows * 256) fail(SP_EINVAL, "leaf inverse: leaf larger than 1024 rows");
     maxn = std::max(maxn, t.n);
   }
+  const bool staged = maxn <= kInvSmemRows;
+  const size_t sm = staged ? (size_t)maxn * (maxn + 1) / 2 * sizeof(double) : 0;
+  if (staged) ensure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_inv_smem), sm);
   for (size_t off = 0; off < tasks.size(); off += 65535) {
     const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
     std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
     DBuf d = upload(part, ctx->stream);
     dim3 grid((maxn + kInvCols - 1) / kInvCols, (unsigned)cnt);
     ProfScope ps(ctx, KID_TRSM);
-    k_leaf_inv<<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
-    check_launch("k_leaf_inv");
+    if (staged) {
+      k_leaf_inv_smem<<<grid, 256, sm, ctx->stream>>>(d.as<LeafTask>());
+      check_launch("k_leaf_inv_smem");
+    } else {
+      k_leaf_inv<<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
+      check_launch("k_leaf_inv");
+    }
   }
+}
+
+void configure_blas_kernels() {
+  configure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf));
+  configure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_inv_smem));
 }
 
 }  // namespace sp

@@ -163,6 +163,17 @@ struct DBuf {
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
 void* dmalloc(size_t bytes, cudaStream_t st);
+// Dynamic shared memory above the 48 KB default.  Each kernel that may need
+// it gets its limit raised once per device, to the opt-in maximum, when the
+// first context on that device is created (configure_*_kernels), before any
+// worker thread launches anything: changing a kernel's attribute while another
+// host thread launches the same kernel made those launches fail.  Launch sites
+// only check their need against the limit (ensure_dynamic_smem, SP_EINVAL).
+void configure_dynamic_smem(const void* func);
+void ensure_dynamic_smem(const void* func, size_t bytes);
+void configure_blas_kernels();
+void configure_lowrank_kernels();
+void configure_param_kernels();
 void dfree(void* p, cudaStream_t st);
 // Copies a host array into a fresh device buffer on the stream.
 template <class T>

@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs, doub
         const double mu = sqrt(x0 * x0 + sigma);
         const double v0 = (x0 <= 0.0) ? x0 - mu : -sigma / (x0 + mu);
         s_tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
-        s_v0 = v0;
+        s_v0 = 1.0 / v0;  // the reciprocal, taken once
         J[j + (int64_t)j * ld] = mu;
       }
       jb.tau[j] = s_tau;
@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(256) k_qr(const QrJob* __restrict__ jobs, doub
     __syncthreads();
     const double tau = s_tau;
     if (tau != 0.0) {
-      const double inv = 1.0 / s_v0;
+      const double inv = s_v0;
       for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) J[i + (int64_t)j * ld] *= inv;
       __syncthreads();
       for (int c = j + 1 + warp; c < R; c += nw) {
@@ -349,14 +349,14 @@ __device__ double make_reflector(double* X, int64_t ld, int j, int rows, double*
       const double mu = sqrt(x0 * x0 + sigma);
       const double v0 = (x0 <= 0.0) ? x0 - mu : -sigma / (x0 + mu);
       s_tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
-      s_v0 = v0;
+      s_v0 = 1.0 / v0;  // the reciprocal, taken once
       X[j + (int64_t)j * ld] = mu;
     }
   }
   __syncthreads();
   const double tau = s_tau;
   if (tau != 0.0) {
-    const double inv = 1.0 / s_v0;
+    const double inv = s_v0;
     for (int i = j + 1 + threadIdx.x; i < rows; i += blockDim.x) X[i + (int64_t)j * ld] *= inv;
   }
   __syncthreads();
@@ -390,6 +390,82 @@ __device__ void apply_reflector(const double* V, int64_t ldv, int j, int rows, d
   }
 }
 
+// One-sided (Hestenes) Jacobi sweeps on the rp columns of B (ld ldb),
+// accumulating the rotations into J, round-robin pair order.  A pair is
+// handled by a group of G lanes (G = 8, 16 or 32 by rp), so one warp works on
+// 32/G pairs at once: for small cores the reductions and the rotation's
+// parameters, not the dot products, are most of a pair's binary64 work.  A
+// pair is rotated when g^2 > eps^2 a b; stops after a sweep without rotation
+// or after max_sweeps.  All threads of the CTA call it.  Returns the flops of
+// the tests and rotations counted by each group's first lane (0 elsewhere).
+template <typename T>
+__device__ double jacobi_sweeps(T* B, T* J, int ldb, int rp, T eps, int max_sweeps, int* s_rot) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int G = rp <= 16 ? 8 : (rp <= 48 ? 16 : 32);
+  const int ppw = 32 / G, grp = lane / G, gl = lane % G;
+  const int P = rp + (rp & 1);
+  const int npairs = P / 2;
+  double fl = 0.0;
+  for (int sweep = 0; sweep < max_sweeps && rp > 1; ++sweep) {
+    if (threadIdx.x == 0) *s_rot = 0;
+    __syncthreads();
+    int rotated = 0;
+    for (int round = 0; round < P - 1; ++round) {
+      for (int base = warp * ppw; base < npairs; base += nw * ppw) {  // uniform within the warp
+        const int pp = base + grp;
+        int i = 0, jj = 0;
+        bool valid = pp < npairs;
+        if (valid) {
+          rr_pair(round, pp, P, i, jj);
+          valid = i < rp && jj < rp;
+        }
+        if (!valid) i = jj = 0;
+        T* gi = B + (int64_t)i * ldb;
+        T* gj = B + (int64_t)jj * ldb;
+        T a = 0, b = 0, g = 0;
+        if (valid)
+          for (int r = gl; r < rp; r += G) {
+            const T x = gi[r], y = gj[r];
+            a = fma(x, x, a);
+            b = fma(y, y, b);
+            g = fma(x, y, g);
+          }
+        for (int o = G >> 1; o > 0; o >>= 1) {  // within the group
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (valid && gl == 0) fl += 6.0 * rp;
+        if (valid && g != (T)0 && g * g > eps * eps * a * b) {
+          if (gl == 0) fl += 12.0 * rp;
+          const T zeta = (b - a) / ((T)2 * g);
+          const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          const T cs = (T)1 / sqrt((T)1 + t * t), sn = cs * t;
+          T* ji = J + (int64_t)i * ldb;
+          T* jj2 = J + (int64_t)jj * ldb;
+          for (int r = gl; r < rp; r += G) {
+            const T x = gi[r], y = gj[r];
+            gi[r] = cs * x - sn * y;
+            gj[r] = sn * x + cs * y;
+            const T u = ji[r], v = jj2[r];
+            ji[r] = cs * u - sn * v;
+            jj2[r] = sn * u + cs * v;
+          }
+          rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (rotated) *s_rot = 1;
+    __syncthreads();
+    const int any = *s_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  return fl;
+}
+
+
 // Truncated SVD of the r_U x r_V core M = R_U R_V^T (one CTA per core):
 //  1. column-pivoted Householder QR  M P = Q1 [R11 R12; 0 R22], stopped when
 //     every remaining column norm is <= 1e-3 tol / sqrt(cols), so the dropped
@@ -419,7 +495,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
   __shared__ int s_rot;
   __shared__ int s_k;
   double nflop = 0.0;   // block-level stages, counted by thread 0
-  double nflopw = 0.0;  // per-warp Jacobi work, counted by each warp's lane 0
+  double nflopw = 0.0;  // Jacobi work, counted by the first lane of each pair group
   // ---- 1. column-pivoted QR of M
   for (int c = warp; c < rv; c += nw) {
     double q = 0.0;
@@ -486,55 +562,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
     J[i + (int64_t)c * ld] = (i == c) ? 1.0 : 0.0;
   }
   __syncthreads();
-  const int P = rp + (rp & 1);
-  const double eps = 1e-15;
-  for (int sweep = 0; sweep < 60 && rp > 1; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    __syncthreads();
-    int rotated = 0;
-    for (int round = 0; round < P - 1; ++round) {
-      for (int pp = warp; pp < P / 2; pp += nw) {
-        int i, jj;
-        rr_pair(round, pp, P, i, jj);
-        if (i >= rp || jj >= rp) continue;
-        double* gi = B + (int64_t)i * ld;
-        double* gj = B + (int64_t)jj * ld;
-        double a = 0.0, b = 0.0, g = 0.0;
-        for (int r = lane; r < rp; r += 32) {
-          const double x = gi[r], y = gj[r];
-          a = fma(x, x, a);
-          b = fma(y, y, b);
-          g = fma(x, y, g);
-        }
-        a = warp_sum(a);
-        b = warp_sum(b);
-        g = warp_sum(g);
-        nflopw += 6.0 * rp;
-        if (g != 0.0 && fabs(g) > eps * sqrt(a * b)) {
-          nflopw += 12.0 * rp;
-          const double zeta = (b - a) / (2.0 * g);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double cs = rsqrt(1.0 + t * t), sn = cs * t;
-          double* ji = J + (int64_t)i * ld;
-          double* jj2 = J + (int64_t)jj * ld;
-          for (int r = lane; r < rp; r += 32) {
-            const double x = gi[r], y = gj[r];
-            gi[r] = cs * x - sn * y;
-            gj[r] = sn * x + cs * y;
-            const double u = ji[r], v = jj2[r];
-            ji[r] = cs * u - sn * v;
-            jj2[r] = sn * u + cs * v;
-          }
-          rotated = 1;
-        }
-      }
-      __syncthreads();
-    }
-    if (rotated && lane == 0) s_rot = 1;
-    __syncthreads();
-    if (!s_rot) break;
-    __syncthreads();
-  }
+  nflopw += jacobi_sweeps<double>(B, J, ld, rp, 1e-15, 60, &s_rot);
   // ---- 4. singular values, order, truncation
   for (int c = warp; c < rp; c += nw) {
     double a = 0.0;
@@ -572,7 +600,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
     __syncthreads();
   }
   // W = Q2 [J(:, perm2); 0] (rv rows) in B's buffer, then S_V = P W
-  double* W = jb.Vacc;
+  double* W = B;
   for (int64_t e = threadIdx.x; e < (int64_t)ld * k; e += blockDim.x) {
     const int r = (int)(e % ld), p = (int)(e / ld);
     W[r + (int64_t)p * ld] = (r < rp) ? J[r + (int64_t)perm2[p] * ld] : 0.0;
@@ -588,7 +616,7 @@ __global__ void __launch_bounds__(1024) k_core_svd(const SvdJob* __restrict__ jo
   }
   if (fc) {
     if (threadIdx.x == 0) nflop += 4.0 * rp * ((double)ru + rv) * k;  // the two reflector applications
-    const double f = (threadIdx.x == 0 ? nflop : 0.0) + (lane == 0 ? nflopw : 0.0);
+    const double f = (threadIdx.x == 0 ? nflop : 0.0) + nflopw;
     if (f > 0.0) atomicAdd(fc, f);
   }
 }
@@ -818,11 +846,11 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
   {
     DBuf d = upload(svd, st);
     const size_t sm = (size_t)maxR * (4 * sizeof(double) + 2 * sizeof(int)) + 64;
-    if (sm > 48 * 1024)
-      check_cuda(cudaFuncSetAttribute(k_core_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                 "smem attr");
+    ensure_dynamic_smem(reinterpret_cast<const void*>(k_core_svd), sm);
     ProfScope ps(ctx, KID_CORE_SVD);
-    k_core_svd<<<(unsigned)nb, 1024, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags, fc_ptr(ctx, KID_CORE_SVD));
+    // small cores: fewer warps make the ~rp barrier-separated stages cheaper
+    const int threads = maxR <= 64 ? 256 : (maxR <= 160 ? 512 : 1024);
+    k_core_svd<<<(unsigned)nb, threads, sm, st>>>(d.as<SvdJob>(), tol, ctx->d_flags, fc_ptr(ctx, KID_CORE_SVD));
     check_launch("k_core_svd");
   }
   // 5. apply reflectors top-down
@@ -834,5 +862,7 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     check_launch("k_apply_q");
   }
 }
+
+void configure_lowrank_kernels() { configure_dynamic_smem(reinterpret_cast<const void*>(k_core_svd)); }
 
 }  // namespace sp

@@ -104,7 +104,9 @@ __global__ void __launch_bounds__(128) k_inertia_warp(const double* __restrict__
     double d = S[sj * W + sj];
     if (fabs(d) < pivmin) d = -pivmin;
     cnt += d < 0.0;
-    const double inv = 1.0 / d;
+    double inv = 0.0;
+    if (lane == 0) inv = 1.0 / d;  // one divide per step, not 32
+    inv = __shfl_sync(0xffffffffu, inv, 0);
     const int lim = (int)((n - 1 - j) < b ? (n - 1 - j) : b);  // rows j+1..j+lim exist
     for (int e = lane; e < lim * lim; e += 32) {
       const int ro = e / lim + 1, co = e % lim + 1;
@@ -274,9 +276,7 @@ void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t
   const double pivmin = DBL_MIN * amax * amax;
   if (b >= 2 && b <= kWarpInertiaMaxB) {
     const size_t sm = (size_t)4 * (b + 1) * (b + 1) * sizeof(double);
-    if (sm > 48 * 1024)
-      check_cuda(cudaFuncSetAttribute(k_inertia_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
-                 "smem attr");
+    ensure_dynamic_smem(reinterpret_cast<const void*>(k_inertia_warp), sm);
     ProfScope ps(ctx, KID_INERTIA);
     k_inertia_warp<<<(nshift + 3) / 4, 128, sm, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev,
                                                                pivmin);
@@ -432,5 +432,7 @@ void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t lda
   *alpha = a;
   *l0 = std::min(dgood / a, 1.0);
 }
+
+void configure_param_kernels() { configure_dynamic_smem(reinterpret_cast<const void*>(k_inertia_warp)); }
 
 }  // namespace sp

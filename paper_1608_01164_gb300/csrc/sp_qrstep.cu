@@ -75,9 +75,10 @@ __device__ __forceinline__ void make_rot(double f, double g, double& c, double& 
 // are addressed by absolute index mod CW = 2b+2; the slot of a column is
 // cleared in every live row as soon as the column is finished, so it is zero
 // when it is reused for column + CW.
-__global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+__global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, int64_t ldab, int64_t n64, int b,
                                                 double mu, double scale, double* __restrict__ cs) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n = (int)n64;  // the host checks n < 2^31
   const int CW = 2 * b + 2;
   double* top = reinterpret_cast<double*>(smem_raw);
   double* r1 = top + (b + 1) * CW;
@@ -85,34 +86,54 @@ __global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, in
   const int lane = threadIdx.x;
   for (int e = lane; e < (2 * b + 2) * CW; e += 32) top[e] = 0.0;
   __syncwarp();
-  // top row r of scale*(A - mu I): columns [r-b, r+b]
-  auto load_top = [&](int64_t r) {
-    double* T = top + (r % (b + 1)) * CW;
-    for (int64_t x = r - b + lane; x <= r + b; x += 32) {
-      if (x < 0 || x >= n) continue;
-      const int64_t d = r - x;
-      const int64_t dd = d < 0 ? -d : d;
-      double v = ab[dd + (d >= 0 ? x : r) * ldab];
-      if (d == 0) v -= mu;
-      T[x % CW] = scale * v;
+  // entries of top row r of scale*(A - mu I) held by this lane: columns
+  // r-b+lane+32h, h = 0..2 (2b+1 <= 65 values per row)
+  auto fetch_top = [&](int r, double* v) {
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      v[h] = 0.0;
+      const int x = r - b + lane + 32 * h;
+      if (r >= n || x < 0 || x >= n || x > r + b) continue;
+      const int d = r - x;
+      const int dd = d < 0 ? -d : d;
+      double a = ab[dd + (int64_t)(d >= 0 ? x : r) * ldab];
+      if (d == 0) a -= mu;
+      v[h] = scale * a;
     }
   };
-  for (int64_t r = 0; r <= b && r < n; ++r) load_top(r);
+  auto store_top = [&](int r, const double* v) {
+    if (r >= n) return;
+    double* T = top + (r % (b + 1)) * CW;
+#pragma unroll
+    for (int h = 0; h < 3; ++h) {
+      const int x = r - b + lane + 32 * h;
+      if (x < 0 || x >= n || x > r + b) continue;
+      T[x % CW] = v[h];
+    }
+  };
+  for (int r = 0; r <= b && r < n; ++r) {
+    double v[3];
+    fetch_top(r, v);
+    store_top(r, v);
+  }
   if (lane == 0) {
     r1[0] = 1.0;
-    for (int64_t t = 1; t <= b && t < n; ++t) bot[(t % b) * CW + (t % CW)] = 1.0;
+    for (int t = 1; t <= b && t < n; ++t) bot[(t % b) * CW + (t % CW)] = 1.0;
   }
   __syncwarp();
   int64_t idx = 0;
   // rotate window rows P (kept) and Q (annihilated in column col) over
-  // absolute columns [col, c_hi]
-  auto rot = [&](double* P, double* Q, int64_t col, int64_t c_lo, int64_t c_hi) {
-    const double f = P[col % CW], g = Q[col % CW];
-    double c, s;
-    make_rot(f, g, c, s);
+  // columns [c_lo, c_hi]
+  auto rot = [&](double* P, double* Q, int col, int c_lo, int c_hi) {
+    const int sc = col % CW;
+    const double f = P[sc], g = Q[sc];
+    double c = 1.0, s = 0.0;
+    if (lane == 0) make_rot(f, g, c, s);  // one lane: binary64 rsqrt is costly
+    c = __shfl_sync(0xffffffffu, c, 0);
+    s = __shfl_sync(0xffffffffu, s, 0);
     __syncwarp();  // every lane has read (f, g) before any lane updates them
-    for (int64_t x = c_lo + lane; x <= c_hi; x += 32) {
-      const int sl = (int)(x % CW);
+    for (int x = c_lo + lane; x <= c_hi; x += 32) {
+      const int sl = x % CW;
       const double u = P[sl], v = Q[sl];
       P[sl] = c * u + s * v;
       Q[sl] = (x == col) ? 0.0 : -s * u + c * v;
@@ -124,22 +145,26 @@ __global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, in
     ++idx;
     __syncwarp();
   };
-  for (int64_t i = 0; i < n; ++i) {
+  // row i+b+1 enters at the end of step i; it is fetched one step ahead
+  double pf[3], nx[3];
+  fetch_top(b + 1, pf);
+  for (int i = 0; i < n; ++i) {
+    fetch_top(i + b + 2, nx);  // in flight during this step's rotations
     double* Ti = top + (i % (b + 1)) * CW;
-    const int64_t chi = mn64(n - 1, i + 2 * b);
+    const int chi = min(n - 1, i + 2 * b);
     if (i >= 1) {
       double* Bi = bot + (i % b) * CW;
-      const int64_t bhi = mn64(n - 1, i + b);
+      const int bhi = min(n - 1, i + b);
       rot(r1, Bi, i, i, bhi);  // alpha_{i,i}
-      const int64_t jmax = mn64(n - 1, i + b - 1);
-      for (int64_t j = i + 1; j <= jmax; ++j) rot(bot + (j % b) * CW, Bi, j, i, bhi);  // alpha_{i,j}
+      const int jmax = min(n - 1, i + b - 1);
+      for (int j = i + 1; j <= jmax; ++j) rot(bot + (j % b) * CW, Bi, j, i, bhi);  // alpha_{i,j}
     }
     rot(Ti, r1, i, i, chi);  // beta_i
-    const int64_t jg = mn64(n - 1, i + b);
-    for (int64_t j = i + 1; j <= jg; ++j) rot(Ti, top + (j % (b + 1)) * CW, i, i, chi);  // gamma_{i,j}
+    const int jg = min(n - 1, i + b);
+    for (int j = i + 1; j <= jg; ++j) rot(Ti, top + (j % (b + 1)) * CW, i, i, chi);  // gamma_{i,j}
     // column i is finished: clear its slot everywhere; retire top row i and
     // bottom row n+i, bring in top row i+b+1 and bottom row n+i+b
-    const int ci = (int)(i % CW);
+    const int ci = i % CW;
     if (lane <= b) top[lane * CW + ci] = 0.0;
     if (lane == 0) r1[ci] = 0.0;
     if (lane < b) bot[lane * CW + ci] = 0.0;
@@ -147,7 +172,9 @@ __global__ void __launch_bounds__(32) k_givens(const double* __restrict__ ab, in
     if (i >= 1)
       for (int x = lane; x < CW; x += 32) bot[(i % b) * CW + x] = 0.0;
     __syncwarp();
-    if (i + b + 1 < n) load_top(i + b + 1);
+    if (i + b + 1 < n) store_top(i + b + 1, pf);
+#pragma unroll
+    for (int h = 0; h < 3; ++h) pf[h] = nx[h];
     if (i >= 1 && lane == 0 && i + b < n) bot[(i % b) * CW + ((i + b) % CW)] = 1.0;
     __syncwarp();
   }
@@ -334,6 +361,7 @@ __global__ void k_corner_blocks(const double* __restrict__ corner, int cs_ld, in
 void givens_generate(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double scale,
                      double* cs_dev) {
   if (b < 1 || b > kMaxB) fail(SP_EINVAL, "bandwidth out of range for the fast QR step");
+  if (n >= ((int64_t)1 << 31)) fail(SP_EINVAL, "fast QR step: n must be below 2^31");
   const size_t sm = sizeof(double) * (size_t)(2 * b + 2) * (2 * b + 2);
   ProfScope ps(ctx, KID_GIVENS);
   k_givens<<<1, 32, sm, ctx->stream>>>(ab_dev, ldab, n, b, mu, scale, cs_dev);

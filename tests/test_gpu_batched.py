@@ -88,3 +88,21 @@ def test_batched_rejects_bad_instance(ctx):
     with pytest.raises(sp.SpError) as ei:
         sp.sp_batched_projector(ctx, [ab, ab], [0.0, 0.0], leaf=3)  # leaf < 2b
     assert ei.value.code == sp.SP_EINVAL
+
+
+def test_batched_concurrent_kernel_limits(ctx):
+    """Instances whose leaves (110..128 rows) need different amounts of dynamic
+    shared memory above the 48 KB default, run on concurrent streams: the
+    per-kernel limit must only ever be raised, never lowered under another
+    stream's launch."""
+    sizes = [7200, 8000, 7600, 7000, 7800, 7400]
+    inst = [(sp_inputs.uniform_band(n, 1, 3100 + i), n // 2) for i, n in enumerate(sizes)]
+    mus = [sp.sp_locate_shift(ctx, ab, nu)[0] for ab, nu in inst]
+    Ps, infos = sp.sp_batched_projector(ctx, [np.ascontiguousarray(ab) for ab, _ in inst], mus, leaf=128,
+                                        tol=1e-10, nstreams=6)
+    try:
+        for (ab, nu), P in zip(inst, Ps):
+            assert round(sp.sp_trace(ctx, P)) == nu
+    finally:
+        for P in Ps:
+            sp.sp_hodlr_destroy(P)
