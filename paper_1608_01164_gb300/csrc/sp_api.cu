@@ -149,7 +149,7 @@ struct Timer {
 // the HODLR inverse factor built during the factorisation.
 sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c, sp_info* inf) {
   Timer t1(ctx->stream);
-  Owned Z(hodlr_mult(ctx, X, X));
+  Owned Z(hodlr_mult(ctx, X, X, true));
   hodlr_scale_shift(ctx, Z.p, c, 1.0);
   inf->ms_mult += t1.stop();
   Timer t2(ctx->stream);
@@ -163,14 +163,13 @@ sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c
   Owned Y(hodlr_mult(ctx, Li.p, X));
   Owned LiT(hodlr_transpose(ctx, Li.p));
   Li.reset(nullptr);
-  Owned V(hodlr_mult(ctx, LiT.p, Y.p));
+  Owned V(hodlr_mult(ctx, LiT.p, Y.p, true));
   Y.reset(nullptr);
   LiT.reset(nullptr);
   inf->ms_solve += t3.stop();
   Timer t4(ctx->stream);
-  Owned Xn(hodlr_add(ctx, b / c, X, a - b / c, V.p, 0.0));
+  Owned Xn(hodlr_add(ctx, b / c, X, a - b / c, V.p, 0.0, true));
   V.reset(nullptr);
-  hodlr_symmetrize(ctx, Xn.p);
   inf->ms_combine += t4.stop();
   return Xn.release();
 }
@@ -185,8 +184,8 @@ sp_hodlr* chol_step(sp_ctx* ctx, const sp_hodlr* X, double a, double b, double c
 // ||R|| ~ 1 - l_k^2 instead of ||X|| ~ 1.
 sp_hodlr* mixed_step(sp_ctx* ctx, const sp_hodlr* X, double a, double c, sp_info* inf) {
   Timer t1(ctx->stream);
-  Owned Z(hodlr_mult(ctx, X, X));
-  Owned R(hodlr_add(ctx, -1.0, Z.p, 0.0, nullptr, 1.0));
+  Owned Z(hodlr_mult(ctx, X, X, true));
+  Owned R(hodlr_add(ctx, -1.0, Z.p, 0.0, nullptr, 1.0, true));
   hodlr_scale_shift(ctx, Z.p, c, 1.0);
   inf->ms_mult += t1.stop();
   Owned D(nullptr);
@@ -203,15 +202,14 @@ sp_hodlr* mixed_step(sp_ctx* ctx, const sp_hodlr* X, double a, double c, sp_info
     Owned Y(hodlr_mult(ctx, Li.p, R.p));
     Owned LiT(hodlr_transpose(ctx, Li.p));
     Li.reset(nullptr);
-    Owned W(hodlr_mult(ctx, LiT.p, Y.p));
+    Owned W(hodlr_mult(ctx, LiT.p, Y.p, true));
     Y.reset(nullptr);
-    D.reset(hodlr_mult(ctx, X, W.p));
+    D.reset(hodlr_mult(ctx, X, W.p, true));
     inf->ms_solve += t3.stop();
   }
   Timer t4(ctx->stream);
-  Owned Xn(hodlr_add(ctx, 1.0, X, a - 1.0, D.p, 0.0));
+  Owned Xn(hodlr_add(ctx, 1.0, X, a - 1.0, D.p, 0.0, true));
   D.reset(nullptr);
-  hodlr_symmetrize(ctx, Xn.p);
   inf->ms_combine += t4.stop();
   return Xn.release();
 }
@@ -219,13 +217,12 @@ sp_hodlr* mixed_step(sp_ctx* ctx, const sp_hodlr* X, double a, double c, sp_info
 // Binary64 Newton-Schulz step for the sign function in residual form:
 // X <- X + X (I - X^2) / 2  (= X (3I - X^2)/2).
 sp_hodlr* newton_schulz_step(sp_ctx* ctx, const sp_hodlr* X) {
-  Owned XX(hodlr_mult(ctx, X, X));
-  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0));
+  Owned XX(hodlr_mult(ctx, X, X, true));
+  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0, true));
   XX.reset(nullptr);
-  Owned D(hodlr_mult(ctx, X, R.p));
+  Owned D(hodlr_mult(ctx, X, R.p, true));
   R.reset(nullptr);
-  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0));
-  hodlr_symmetrize(ctx, Xn.p);
+  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0, true));
   return Xn.release();
 }
 
@@ -235,22 +232,21 @@ sp_hodlr* newton_schulz_step(sp_ctx* ctx, const sp_hodlr* X) {
 // error scales with ||R||, which the iteration drives to zero.
 sp_hodlr* newton_schulz_step_mixed(sp_ctx* ctx, const sp_hodlr* X, sp_info* inf) {
   Timer t1(ctx->stream);
-  Owned XX(hodlr_mult(ctx, X, X));
-  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0));
+  Owned XX(hodlr_mult(ctx, X, X, true));
+  Owned R(hodlr_add(ctx, -1.0, XX.p, 0.0, nullptr, 1.0, true));
   XX.reset(nullptr);
   inf->ms_mult += t1.stop();
   Owned D(nullptr);
   {
     Fp32Gemms fp32(ctx);
     Timer t2(ctx->stream);
-    D.reset(hodlr_mult(ctx, X, R.p));
+    D.reset(hodlr_mult(ctx, X, R.p, true));
     inf->ms_solve += t2.stop();
   }
   R.reset(nullptr);
   Timer t3(ctx->stream);
-  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0));
+  Owned Xn(hodlr_add(ctx, 1.0, X, 0.5, D.p, 0.0, true));
   D.reset(nullptr);
-  hodlr_symmetrize(ctx, Xn.p);
   inf->ms_combine += t3.stop();
   return Xn.release();
 }
@@ -263,11 +259,10 @@ sp_hodlr* qr_step(sp_ctx* ctx, const sp_hodlr* A, double alpha, double a, double
   Owned Q1(q1), Q2(q2);
   Owned Q2t(hodlr_transpose(ctx, Q2.p));
   Q2.reset(nullptr);
-  Owned P(hodlr_mult(ctx, Q1.p, Q2t.p));
+  Owned P(hodlr_mult(ctx, Q1.p, Q2t.p, true));
   Q1.reset(nullptr);
   Q2t.reset(nullptr);
-  Owned X1(hodlr_add(ctx, (b / c) / alpha, A, (a - b / c) / sc, P.p, 0.0));
-  hodlr_symmetrize(ctx, X1.p);
+  Owned X1(hodlr_add(ctx, (b / c) / alpha, A, (a - b / c) / sc, P.p, 0.0, true));
   return X1.release();
 }
 

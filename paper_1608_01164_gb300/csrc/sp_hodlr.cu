@@ -262,6 +262,11 @@ __global__ void k_swap_sibling_ranks(const int* __restrict__ src, int* dst, int 
   for (int c = 2 + blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) dst[c] = src[c ^ 1];
 }
 
+__global__ void k_mirror_ranks(int* rank, int nodes) {
+  const int s = 3 + 2 * (blockIdx.x * blockDim.x + threadIdx.x);  // right children 3, 5, 7, ...
+  if (s < nodes) rank[s] = rank[s - 1];
+}
+
 __global__ void k_set_int(int* p, int v) {
   if (threadIdx.x == 0) *p = v;
 }
@@ -432,14 +437,18 @@ void hodlr_apply_sub(sp_ctx* ctx, const sp_hodlr* M, int c, const double* X, int
 }
 
 // --------------------------------------------------------------------- add --
-sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma) {
+static void mirror_right(sp_ctx* ctx, sp_hodlr* M);
+static void symmetrize_leaves(sp_ctx* ctx, sp_hodlr* M);
+
+sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma,
+                    bool symmetric) {
   const int cap = B ? std::max(A->cap, B->cap) : A->cap;
   sp_hodlr* C = hodlr_alloc(ctx, A->tree, cap, A->tol);
   try {
     hodlr_set_zero(ctx, C);
     const Tree& T = *A->tree;
     std::vector<LrBlock> blocks;
-    for (int c = 2; c < T.nodes(); ++c) {
+    for (int c = 2; c < T.nodes(); c += symmetric ? 2 : 1) {
       LrBlock lb;
       lb.m = (int)T.sz[c];
       lb.q = (int)T.sz[c ^ 1];
@@ -466,6 +475,10 @@ sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, c
         lt.push_back(AxpbyTask{B->leaf(j), C->leaf(j), B->leaf_ld, C->leaf_ld, s, s, nullptr, nullptr, beta, 1.0, 0.0});
       }
       axpby_batched(ctx, lt);
+    }
+    if (symmetric) {
+      mirror_right(ctx, C);
+      symmetrize_leaves(ctx, C);
     }
   } catch (...) {
     hodlr_free(C);
@@ -506,10 +519,31 @@ sp_hodlr* hodlr_transpose(sp_ctx* ctx, const sp_hodlr* M) {
 
 // M <- (M + M^T)/2: leaves symmetrised, each left-child block recompressed
 // from [U_c | V_s][V_c | U_s]^T / 2 and mirrored into the right sibling.
+// Right children from left children for a symmetric matrix: B_s = B_c^T, so
+// U_s = V_c (rows I_s) and V_s = U_c (rows I_c) -- one batched copy -- and
+// rank[s] = rank[c].  Leaves are symmetrised separately.
+static void mirror_right(sp_ctx* ctx, sp_hodlr* M) {
+  const Tree& T = *M->tree;
+  if (T.L == 0) return;
+  std::vector<AxpbyTask> cp;
+  for (int c = 2; c < T.nodes(); c += 2) {
+    const int s = c + 1;
+    cp.push_back(AxpbyTask{M->Vc(c), M->Uc(s), T.n, T.n, (int)T.sz[s], M->cap, nullptr, nullptr, 1.0, 0.0, 0.0});
+    cp.push_back(AxpbyTask{M->Uc(c), M->Vc(s), T.n, T.n, (int)T.sz[c], M->cap, nullptr, nullptr, 1.0, 0.0, 0.0});
+  }
+  axpby_batched(ctx, cp);
+  k_mirror_ranks<<<(T.nodes() + 255) / 256, 256, 0, ctx->stream>>>(M->rank, T.nodes());
+  check_launch("k_mirror_ranks");
+}
+
+static void symmetrize_leaves(sp_ctx* ctx, sp_hodlr* M) {
+  k_leaf_symmetrize<<<M->tree->nleaves(), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld);
+  check_launch("k_leaf_symmetrize");
+}
+
 void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M) {
   const Tree& T = *M->tree;
-  k_leaf_symmetrize<<<T.nleaves(), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld);
-  check_launch("k_leaf_symmetrize");
+  symmetrize_leaves(ctx, M);
   if (T.L == 0) return;
   std::vector<LrBlock> blocks;
   for (int c = 2; c < T.nodes(); c += 2) {
@@ -527,24 +561,11 @@ void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M) {
     blocks.push_back(lb);
   }
   recompress(ctx, blocks, M->tol);
-  // right sibling s = c+1: U_s = V_c (rows I_s), V_s = U_c (rows I_c)
-  for (int l = 1; l <= T.L; ++l) {
-    for (int c = 1 << l; c < (2 << l); c += 2) {
-      const int s = c + 1;
-      check_cuda(cudaMemcpy2DAsync(M->Uc(s), sizeof(double) * T.n, M->Vc(c), sizeof(double) * T.n,
-                                   sizeof(double) * T.sz[s], M->cap, cudaMemcpyDeviceToDevice, ctx->stream),
-                 "mirror");
-      check_cuda(cudaMemcpy2DAsync(M->Vc(s), sizeof(double) * T.n, M->Uc(c), sizeof(double) * T.n,
-                                   sizeof(double) * T.sz[c], M->cap, cudaMemcpyDeviceToDevice, ctx->stream),
-                 "mirror");
-      check_cuda(cudaMemcpyAsync(M->rank + s, M->rank + c, sizeof(int), cudaMemcpyDeviceToDevice, ctx->stream),
-                 "mirror rank");
-    }
-  }
+  mirror_right(ctx, M);
 }
 
 // ---------------------------------------------------------------- product ---
-sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
+sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B, bool symmetric) {
   if (!same_tree(*A->tree, *B->tree)) fail(SP_EINVAL, "hodlr_mult: operands on different trees");
   const Tree& T = *A->tree;
   const int L = T.L;
@@ -592,7 +613,7 @@ sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
     }
     // off-diagonal blocks of C
     std::vector<LrBlock> blocks;
-    for (int c = 2; c < T.nodes(); ++c) {
+    for (int c = 2; c < T.nodes(); c += symmetric ? 2 : 1) {
       const int s = c ^ 1;
       const int l = Tree::level_of(c);
       LrBlock lb;
@@ -631,6 +652,10 @@ sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B) {
                         1.0, nullptr, nullptr, B->rank + (ap ^ 1)));
       }
       gemm_batched(ctx, false, true, lt);
+    }
+    if (symmetric) {
+      mirror_right(ctx, C);
+      symmetrize_leaves(ctx, C);
     }
   } catch (...) {
     hodlr_free(C);

@@ -298,8 +298,13 @@ sp_hodlr* hodlr_from_band(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, i
                           double tol, int cap);
 void hodlr_to_dense(sp_ctx* ctx, const sp_hodlr* M, int64_t row0, int64_t nrows, double* out, int64_t ld);
 double hodlr_trace(sp_ctx* ctx, const sp_hodlr* M);
-sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma);
-sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B);
+// symmetric = true: the caller knows the result is symmetric (up to rounding
+// and truncation); only the left child of every sibling pair is recompressed,
+// the right one is its transpose (half the recompression work), and the
+// leaves are symmetrised.
+sp_hodlr* hodlr_add(sp_ctx* ctx, double alpha, const sp_hodlr* A, double beta, const sp_hodlr* B, double gamma,
+                    bool symmetric = false);
+sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B, bool symmetric = false);
 sp_hodlr* hodlr_cholesky(sp_ctx* ctx, const sp_hodlr* Z);
 // H-Cholesky returning both the factor L and its HODLR inverse L^{-1}.
 void hodlr_cholesky_inv(sp_ctx* ctx, const sp_hodlr* Z, sp_hodlr** L, sp_hodlr** Li);

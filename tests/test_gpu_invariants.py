@@ -1,4 +1,4 @@
-"""Projectors beyond the oracle's reach, judged by invariants that hold at any
+"""Projectors beyond the oracle's reach, checked by invariants that hold at any
 size: trace = nu exactly after rounding (nu from an inertia count),
 idempotence P(Pv) = Pv, commutation A(Pv) = P(Av) and symmetry
 <u, Pv> = <Pu, v> on seeded probe vectors (Sec. 2: Pi is the orthogonal
