@@ -320,42 +320,6 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
   }
 }
 
-// X <- L^{-1} X or L^{-T} X for a lower-triangular leaf L; CTA = (task, 64
-// right-hand-side columns).
-template <bool TRANS>
-__global__ void __launch_bounds__(256) k_leaf_trsm(const LeafTask* __restrict__ tasks) {
-  const LeafTask t = tasks[blockIdx.y];
-  const int w = dsize(t.w, t.pw);
-  const int c0 = blockIdx.x * 64;
-  if (c0 >= w) return;
-  const int nc = min(64, w - c0);
-  const int n = t.n;
-  const double* L = t.A;
-  const int64_t lda = t.lda;
-  double* X = t.X + (int64_t)c0 * t.ldx;
-  const int64_t ldx = t.ldx;
-  for (int s = 0; s < n; ++s) {
-    const int j = TRANS ? n - 1 - s : s;
-    const double inv = 1.0 / L[j + (int64_t)j * lda];
-    for (int c = threadIdx.x; c < nc; c += blockDim.x) X[j + (int64_t)c * ldx] *= inv;
-    __syncthreads();
-    if (!TRANS) {
-      const int m = n - j - 1;
-      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        const int i = j + 1 + e % m, c = e / m;
-        X[i + (int64_t)c * ldx] -= L[i + (int64_t)j * lda] * X[j + (int64_t)c * ldx];
-      }
-    } else {
-      const int m = j;
-      for (int e = threadIdx.x; e < m * nc; e += blockDim.x) {
-        const int i = e % m, c = e / m;
-        X[i + (int64_t)c * ldx] -= L[j + (int64_t)i * lda] * X[j + (int64_t)c * ldx];
-      }
-    }
-    __syncthreads();
-  }
-}
-
 // Li = L^{-1} for a lower-triangular leaf L (n <= kInvRows * 256).  CTA =
 // (block of kInvCols identity columns, task); forward substitution L X = I
 // restricted to those columns, which are zero above their first column c0,
@@ -593,25 +557,6 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   check_launch("k_leaf_potrf");
 }
 
-void leaf_trsm(sp_ctx* ctx, bool trans, const std::vector<LeafTask>& tasks) {
-  if (tasks.empty()) return;
-  int maxw = 1;
-  for (const auto& t : tasks) {
-    maxw = std::max(maxw, t.w);
-    ctx->flops += (double)t.n * t.n * t.w;
-  }
-  for (size_t off = 0; off < tasks.size(); off += 65535) {
-    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
-    std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
-    DBuf d = upload(part, ctx->stream);
-    dim3 grid((maxw + 63) / 64, (unsigned)cnt);
-    ProfScope ps(ctx, KID_TRSM);
-    if (trans) k_leaf_trsm<true><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
-    else k_leaf_trsm<false><<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
-    check_launch("k_leaf_trsm");
-  }
-}
-
 void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   if (tasks.empty()) return;
   int maxn = 0;
@@ -627,7 +572,7 @@ void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
     std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
     DBuf d = upload(part, ctx->stream);
     dim3 grid((maxn + kInvCols - 1) / kInvCols, (unsigned)cnt);
-    ProfScope ps(ctx, KID_TRSM);
+    ProfScope ps(ctx, KID_LEAF_INV);
     if (staged) {
       k_leaf_inv_smem<<<grid, 256, sm, ctx->stream>>>(d.as<LeafTask>());
       check_launch("k_leaf_inv_smem");

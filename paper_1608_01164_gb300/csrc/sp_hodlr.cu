@@ -541,29 +541,6 @@ static void symmetrize_leaves(sp_ctx* ctx, sp_hodlr* M) {
   check_launch("k_leaf_symmetrize");
 }
 
-void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M) {
-  const Tree& T = *M->tree;
-  symmetrize_leaves(ctx, M);
-  if (T.L == 0) return;
-  std::vector<LrBlock> blocks;
-  for (int c = 2; c < T.nodes(); c += 2) {
-    const int s = c + 1;
-    LrBlock lb;
-    lb.m = (int)T.sz[c];
-    lb.q = (int)T.sz[s];
-    lb.segs.push_back(Seg{M->Uc(c), M->Vc(c), T.n, T.n, M->cap, M->rank + c, 0.5});
-    lb.segs.push_back(Seg{M->Vc(s), M->Uc(s), T.n, T.n, M->cap, M->rank + s, 0.5});
-    lb.Uout = M->Uc(c);
-    lb.Vout = M->Vc(c);
-    lb.ldu_out = lb.ldv_out = T.n;
-    lb.rank_out = M->rank + c;
-    lb.cap = M->cap;
-    blocks.push_back(lb);
-  }
-  recompress(ctx, blocks, M->tol);
-  mirror_right(ctx, M);
-}
-
 // ---------------------------------------------------------------- product ---
 sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B, bool symmetric) {
   if (!same_tree(*A->tree, *B->tree)) fail(SP_EINVAL, "hodlr_mult: operands on different trees");
@@ -666,7 +643,11 @@ sp_hodlr* hodlr_mult(sp_ctx* ctx, const sp_hodlr* A, const sp_hodlr* B, bool sym
 
 // ------------------------------------------------- subtree low-rank update --
 // M_sub(c) += alpha * Ul Ur^T with Ul, Ur: |I_c| x w (pointers at row lo[c],
-// leading dimensions ldl, ldr), width *pw (device) capped by w.
+// leading dimensions ldl, ldr), width *pw (device) capped by w.  Used for the
+// Schur complements of the H-Cholesky, which only ever reads the lower block
+// of a node (owned by its right child) and zeroes the upper one (owned by the
+// left child) when the node is factored: only right children's blocks and the
+// leaves are updated.
 static void lr_update_sub(sp_ctx* ctx, sp_hodlr* M, int c, const double* Ul, int64_t ldl, const double* Ur,
                           int64_t ldr, int w, const int* pw, double alpha) {
   const Tree& T = *M->tree;
@@ -676,7 +657,7 @@ static void lr_update_sub(sp_ctx* ctx, sp_hodlr* M, int c, const double* Ul, int
   std::vector<LrBlock> blocks;
   for (int l = lc + 1; l <= L; ++l) {
     const int d0 = c << (l - lc);
-    for (int d = d0; d < d0 + (1 << (l - lc)); ++d) {
+    for (int d = d0 + 1; d < d0 + (1 << (l - lc)); d += 2) {
       const int s = d ^ 1;
       LrBlock lb;
       lb.m = (int)T.sz[d];

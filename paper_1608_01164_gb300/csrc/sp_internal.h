@@ -75,7 +75,7 @@ struct sp_hodlr {
 namespace sp {
 // Kernel families timed and flop-counted by the profiler.
 enum KernelId {
-  KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_CORE_SVD, KID_GATHER, KID_POTRF, KID_TRSM, KID_GIVENS, KID_REPLAY_LEAF,
+  KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_CORE_SVD, KID_GATHER, KID_POTRF, KID_LEAF_INV, KID_GIVENS, KID_REPLAY_LEAF,
   KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_HOST_WAIT, KID_COUNT
 };
 }  // namespace sp
@@ -245,8 +245,6 @@ struct LeafTask {
 // In-place lower Cholesky of each leaf (upper triangle zeroed); sets the
 // breakdown flag on a non-positive pivot.
 void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
-// X <- L^{-1} X (trans = false) or L^{-T} X (trans = true), L lower.
-void leaf_trsm(sp_ctx* ctx, bool trans, const std::vector<LeafTask>& tasks);
 // X <- L^{-1} (the whole n x n inverse) for lower-triangular leaves, n <= 1024.
 void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 
@@ -310,7 +308,6 @@ sp_hodlr* hodlr_cholesky(sp_ctx* ctx, const sp_hodlr* Z);
 void hodlr_cholesky_inv(sp_ctx* ctx, const sp_hodlr* Z, sp_hodlr** L, sp_hodlr** Li);
 sp_hodlr* hodlr_tri_inverse(sp_ctx* ctx, const sp_hodlr* L);
 sp_hodlr* hodlr_trsm(sp_ctx* ctx, const sp_hodlr* L, bool trans, const sp_hodlr* B);
-void hodlr_symmetrize(sp_ctx* ctx, sp_hodlr* M);
 sp_hodlr* hodlr_transpose(sp_ctx* ctx, const sp_hodlr* M);
 
 // Inertia counts and the QR-based first step.
