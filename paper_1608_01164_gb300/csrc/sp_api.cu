@@ -11,6 +11,9 @@
 //          (the paper's (X W^{-1}) W^{-*} with W = L^T, evaluated as two
 //          formatted left solves since X and Z commute and are symmetric)
 //   stop when |1 - l_k| <= delta; P = (I - X)/2.
+// Mixed precision (not in the paper): late Cholesky steps in residual form
+// with binary32 GEMMs (SP_MIXED_FP32), or late steps replaced by residual
+// Newton-Schulz steps (SP_MIXED_NS); binary64 polish at the end.
 // The iteration count depends only on the scalars, so the host runs the
 // scalar recurrence and every matrix operation stays on the device.
 #include <algorithm>

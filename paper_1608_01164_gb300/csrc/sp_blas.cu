@@ -1,6 +1,6 @@
 // sp_blas.cu -- dense building blocks of the HODLR arithmetic: batched
-// binary64 GEMM with device-side sizes, leaf Cholesky and triangular solves,
-// and small strided element-wise kernels.  Every kernel takes a task list so
+// binary64 (and binary32) GEMM with device-side sizes, leaf Cholesky, leaf
+// inverses, and small strided element-wise kernels.  Every kernel takes a task list so
 // that one launch covers all blocks of one kind across the HODLR tree.
 //
 // Roofline note: on GB300 binary64 runs at ~1.2 TFLOP/s (8 GFLOP/s per SM)

@@ -16,10 +16,11 @@
 // and the whole product is: L restricted applies, two coupling GEMMs, one
 // batched recompression of all blocks, and leaf GEMMs.  Cost O(k^2 n log^2 n).
 //
-// H-Cholesky and the triangular solves are recursive (the factor of the
-// trailing block needs the Schur complement of everything before it); each
-// recursion step enqueues batched kernels (subtree low-rank updates, skinny
-// solves) without host synchronisation.
+// H-Cholesky is recursive (the factor of the trailing block needs the Schur
+// complement of everything before it); each recursion step enqueues batched
+// kernels (subtree low-rank updates, products with the inverse factor built
+// along the way).  Triangular solves with a HODLR right-hand side are products
+// with that inverse.
 #include <algorithm>
 #include <cmath>
 #include <cstring>

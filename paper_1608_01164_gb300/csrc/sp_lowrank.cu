@@ -13,12 +13,15 @@
 //      compactly: its row count and the children's row offsets follow from the
 //      actual width R on the device, so no stage works on padding;
 //   3. core  M = R_U R_V^T  (r_U x r_V, r = min(rows, R));
-//   4. one-sided (Hestenes) Jacobi SVD of M in one CTA, round-robin pair order;
+//   4. truncated SVD of M in one CTA (k_core_svd): column-pivoted QR stopped at
+//      the truncation level, QR of the transposed trapezoid, one-sided Jacobi
+//      on the kept triangle (pairs on lane groups);
 //   5. keep the k singular values > tol, U = Q_U [U~_k S_k; 0],
 //      V = Q_V [V~_k; 0] by applying the Householder reflectors back down the
 //      tree.
-// All sizes except the static upper bounds are device-resident (ranks produced
-// by earlier launches), so the whole pipeline is enqueued without a host sync.
+// The segments' widths are ranks produced by earlier launches; one read-back
+// per call (the only host synchronisation) sizes every buffer, chunk and slot
+// by the actual width R; the kernels read the same widths on the device.
 #include <algorithm>
 #include <chrono>
 #include <cmath>

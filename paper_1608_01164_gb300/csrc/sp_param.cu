@@ -4,11 +4,12 @@
 // (Sec. 5, Eq. (param_estimation)).  QDWH needs alpha >= ||A - mu I||_2 and
 // l0 <= sigma_min((A - mu I)/alpha); both follow from eigenvalue brackets, and
 // brackets follow from inertia counts nu(sigma) = #{lambda < sigma}
-// (Sylvester's law of inertia on A - sigma I = L D L^T).  Each thread counts
-// one shift: the tridiagonal Sturm recurrence d_i = (a_i - sigma) -
-// e_{i-1}^2 / d_{i-1}, or for b > 1 the unpivoted banded LDL^T with the last b
-// columns of L kept in a per-thread ring.  A count is a sequential chain of n
-// dependent divisions (latency-bound), so many shifts run side by side.
+// (Sylvester's law of inertia on A - sigma I = L D L^T).  Tridiagonal: one
+// thread per shift runs the Sturm recurrence d_i = (a_i - sigma) -
+// e_{i-1}^2 / d_{i-1}.  Banded, 2 <= b <= 80: one warp per shift runs the
+// unpivoted banded LDL^T with the (b+1)^2 Schur window in shared memory; wider
+// bands: one thread per shift with the last b columns of L in a ring.  A count
+// is a sequential chain of n dependent steps, so many shifts run side by side.
 #include <algorithm>
 #include <cfloat>
 #include <cmath>
