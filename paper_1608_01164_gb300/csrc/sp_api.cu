@@ -335,6 +335,8 @@ void sp_ctx_destroy(sp_ctx_t ctx) {
       cudaEventDestroy(e.first);
       cudaEventDestroy(e.second);
     }
+  for (auto& ne : ctx->chol_ev)
+    for (int k = 0; k < ne.nev; ++k) cudaEventDestroy(ne.e[k]);
   delete ctx;
 }
 
