@@ -49,3 +49,13 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     # null context -> SP_EINVAL before any device work
     assert lib.sp_hodlr_from_band(None, 10, 1, None, 2, 0.0, 4, 1e-10, 0, ctypes.byref(h)) == sp.SP_EINVAL
     assert lib.sp_qdwh_sign(None, None, None, None, None) == sp.SP_EINVAL
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """No fallback: without the built library, loading raises."""
+    monkeypatch.setattr(sp, "LIB_PATH", str(tmp_path / "libsp.so"))
+    monkeypatch.setattr(sp, "_lib", None)
+    with pytest.raises(OSError, match="missing"):
+        sp.load()
+    with pytest.raises(OSError):
+        sp.sp_ctx_create(0)
