@@ -128,6 +128,70 @@ def dense_from_band(ab: np.ndarray) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Banded matrices with a prescribed spectrum (the paper's synthetic test
+# matrices, Sec. 6.1): an orthogonal similarity of diag(lambda) by Givens
+# rotations, with the fill-in outside the band chased to the bottom-right
+# corner.  Input construction only; nothing of the projector method.
+# --------------------------------------------------------------------------
+
+def gap_spectrum(n: int, gap: float, seed: int) -> np.ndarray:
+    """n eigenvalues uniform in [-1, -gap] (first n/2) and [gap, 1] (the rest),
+    so that mu = 0 separates the lower n/2 from the upper ones."""
+    k = n // 2
+    lo = uniform(seed, k, gap, 1.0)
+    hi = uniform(seed, n - k, gap, 1.0, offset=k)
+    return np.concatenate([-lo, hi])
+
+
+def _rotate(A: np.ndarray, p: int, c: float, s: float, lo: int, hi: int) -> None:
+    """A <- G^T A G for the rotation G acting on indices p, p+1 as
+    [[c, -s], [s, c]] (G^T [x, y] = [c x + s y, -s x + c y]); rows and columns
+    are touched only over [lo, hi)."""
+    rows = A[p:p + 2, lo:hi]
+    x, y = rows[0].copy(), rows[1].copy()
+    rows[0] = c * x + s * y
+    rows[1] = -s * x + c * y
+    cols = A[lo:hi, p:p + 2]
+    x, y = cols[:, 0].copy(), cols[:, 1].copy()
+    cols[:, 0] = c * x + s * y
+    cols[:, 1] = -s * x + c * y
+
+
+def prescribed_band(lam: np.ndarray, b: int) -> np.ndarray:
+    """Symmetric b-banded matrix with eigenvalues lam, in lower band storage.
+
+    For i = n-1, ..., 1 (0-based pair (i-1, i)): the rotation that annihilates
+    the second component of [a_ii, 1]^T is applied as a similarity on rows and
+    columns i-1, i; the entry it creates b+1 below the diagonal is chased down
+    by rotations on (k-1, k) that annihilate it, each moving the bulge b rows
+    further, until it leaves the matrix.  Dense O(n^2) storage, O(b) work per
+    rotation: meant for n up to a few thousand."""
+    lam = np.asarray(lam, dtype=np.float64)
+    n = lam.shape[0]
+    A = np.diag(lam)
+    w = b + 2  # band plus one bulge on each side of the touched indices
+    for i in range(n - 1, 0, -1):
+        x = A[i, i]
+        r = math.hypot(x, 1.0)
+        c, s = x / r, 1.0 / r
+        p = i - 1
+        _rotate(A, p, c, s, max(0, p - w), min(n, p + 2 + w))
+        k, m = p + 1 + b, p  # the bulge A[k, m] below the band
+        while k < n:
+            f, g = A[k - 1, m], A[k, m]
+            if g != 0.0:
+                r = math.hypot(f, g)
+                c, s = f / r, g / r
+                _rotate(A, k - 1, c, s, max(0, k - 1 - w), min(n, k + 1 + w))
+                A[k, m] = A[m, k] = 0.0
+            k, m = k + b, k - 1
+    ab = np.zeros((n, b + 1))
+    for d in range(b + 1):
+        ab[: n - d, d] = np.diagonal(A, -d)
+    return ab
+
+
+# --------------------------------------------------------------------------
 # The five workloads.  Each returns a list of (name, ab, nu) instances; the
 # shift mu is located separately (by inertia counts) from nu.
 # --------------------------------------------------------------------------

@@ -55,3 +55,19 @@ def test_workload_recipes():
     (_, a2, _), = sp_inputs.workload(1, n=512)
     assert np.array_equal(a1, a2)
     assert not np.array_equal(sp_inputs.uniform_band(300, 2, 1), sp_inputs.uniform_band(300, 2, 2))
+
+
+def test_prescribed_spectrum_band():
+    """Sec. 6.1 construction: the band reproduces the prescribed eigenvalues,
+    has exactly b diagonals below the main one, and is populated."""
+    for n, b, gap in [(120, 1, 1e-1), (200, 3, 1e-3), (300, 8, 1e-6)]:
+        lam = sp_inputs.gap_spectrum(n, gap, 11)
+        assert np.sum(lam < 0) == n // 2
+        assert np.all(np.abs(lam) >= gap) and np.all(np.abs(lam) <= 1.0)
+        ab = sp_inputs.prescribed_band(lam, b)
+        assert ab.shape == (n, b + 1)
+        w = np.linalg.eigvalsh(sp_inputs.dense_from_band(ab))
+        assert np.max(np.abs(w - np.sort(lam))) < 1e-12
+        assert np.mean(ab[: n - b, b] != 0.0) > 0.7
+        assert np.all(ab[: n - 1, 1] != 0.0)
+        assert np.all(ab[n - b:, b] == 0.0)  # padding outside the matrix
