@@ -134,13 +134,14 @@ def dense_from_band(ab: np.ndarray) -> np.ndarray:
 # corner.  Input construction only; nothing of the projector method.
 # --------------------------------------------------------------------------
 
-def gap_spectrum(n: int, gap: float, seed: int) -> np.ndarray:
-    """n eigenvalues uniform in [-1, -gap] (first n/2) and [gap, 1] (the rest),
-    so that mu = 0 separates the lower n/2 from the upper ones."""
+def gap_spectrum(n: int, gap: float) -> np.ndarray:
+    """n eigenvalues equispaced in [-1, -gap] (first n/2) and [gap, 1] (the
+    rest), endpoints included, so that mu = 0 separates the lower n/2 from the
+    upper ones and the spectral gap at mu is exactly 2 gap."""
     k = n // 2
-    lo = uniform(seed, k, gap, 1.0)
-    hi = uniform(seed, n - k, gap, 1.0, offset=k)
-    return np.concatenate([-lo, hi])
+    lo = np.linspace(gap, 1.0, k) if k > 1 else np.full(k, gap)
+    hi = np.linspace(gap, 1.0, n - k) if n - k > 1 else np.full(n - k, gap)
+    return np.concatenate([-lo[::-1], hi])
 
 
 def _rotate(A: np.ndarray, p: int, c: float, s: float, lo: int, hi: int) -> None:

@@ -61,9 +61,10 @@ def test_prescribed_spectrum_band():
     """Sec. 6.1 construction: the band reproduces the prescribed eigenvalues,
     has exactly b diagonals below the main one, and is populated."""
     for n, b, gap in [(120, 1, 1e-1), (200, 3, 1e-3), (300, 8, 1e-6)]:
-        lam = sp_inputs.gap_spectrum(n, gap, 11)
+        lam = sp_inputs.gap_spectrum(n, gap)
         assert np.sum(lam < 0) == n // 2
         assert np.all(np.abs(lam) >= gap) and np.all(np.abs(lam) <= 1.0)
+        assert np.min(np.abs(lam)) == gap and np.max(np.abs(lam)) == 1.0  # the gap is attained
         ab = sp_inputs.prescribed_band(lam, b)
         assert ab.shape == (n, b + 1)
         w = np.linalg.eigvalsh(sp_inputs.dense_from_band(ab))
