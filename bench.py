@@ -56,6 +56,9 @@ def parse(argv=None):
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample-n", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--mixed-steps", type=int, default=2,
+                   help="timed steps of the mixed-precision (Newton-Schulz tail) form measured beside the binary64 "
+                        "run, with ||P_mixed - P_fp64||_2 by power iteration (0: skip)")
     return p.parse_args(argv)
 
 
@@ -164,6 +167,54 @@ def run_reference(args):
             "e2e": {"value": v, "unit": "s/projector", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+# ------------------------------------------------------ accuracy, roofline --
+
+def diff_norm2(sp, ctx, P1, P2, n, steps=30, s=4, seed=99):
+    """||P1 - P2||_2 by block power iteration on the symmetric difference
+    through sp_apply (device operands); a lower bound converging to the norm."""
+    import torch
+    X = torch.from_numpy(sp_inputs.normal(seed, n * s).reshape(s, n)).cuda()  # rows = columns of n x s
+    Y1 = torch.empty_like(X)
+    Y2 = torch.empty_like(X)
+    est = 0.0
+    for _ in range(steps):
+        q, _ = torch.linalg.qr(X.T)
+        X = q.T.contiguous()
+        sp.sp_apply(ctx, P1, s, X, n, Y1, n)
+        sp.sp_apply(ctx, P2, s, X, n, Y2, n)
+        X = Y1 - Y2
+        est = max(est, float(torch.linalg.norm(X, dim=1).max()))
+    return est
+
+
+def kernel_table(prof, givens_rotations):
+    """Per kernel family: launches, ms, share of device time, counted GFLOP and
+    the fraction of the binary64 rate; latency-bound chains report their
+    critical path per unit instead."""
+    fam = {}
+    for k, (la, ms_k, fl) in prof.items():
+        if k == "host_wait" or la == 0:
+            continue
+        base = k.split("[")[0] if k.startswith("k_gemm") and "fp32" not in k else k
+        a = fam.setdefault(base, [0, 0.0, 0.0])
+        a[0] += la
+        a[1] += ms_k
+        a[2] += fl
+    total = max(sum(v[1] for v in fam.values()), 1e-9)
+    out = {}
+    for k, (la, ms_k, fl) in sorted(fam.items(), key=lambda kv: -kv[1][1]):
+        e = {"launches": la, "ms": round(ms_k, 3), "share": round(ms_k / total, 4), "gflop": round(fl / 1e9, 3)}
+        if fl > 0 and ms_k > 0:
+            tf = fl / (ms_k * 1e-3) / 1e12
+            e["tflops"] = round(tf, 4)
+            e["frac_fp64"] = round(tf / FP64_PEAK_TFLOPS, 4)
+        if k == "k_givens" and givens_rotations:
+            e["ns_per_rotation"] = round(ms_k * 1e6 / givens_rotations, 1)
+            e["bound"] = "latency: one dependent chain of rotations (critical path = ms)"
+        out[k] = e
+    return out
 
 
 # ---------------------------------------------------------------- clocks ----
@@ -310,23 +361,59 @@ def run_ours(args):
         e2e.append(time.perf_counter() - t0)
     e2e_s = max_over_ranks(float(np.mean(e2e)) if e2e else None, world, "cuda")
     # dominant kernel by device time; the k_gemm call-site buckets are one kernel
-    per_kernel = {}
-    for k, (la, ms_k, fl) in prof.items():
-        if k == "host_wait":  # host time blocked at syncs, not a kernel
-            continue
-        base = k.split("[")[0]
-        a = per_kernel.setdefault(base, [0, 0.0, 0.0])
-        a[0] += la
-        a[1] += ms_k
-        a[2] += fl
-    kname, (kl, kms, kfl) = max(per_kernel.items(), key=lambda kv: kv[1][1])
+    b = ab.shape[1] - 1
+    n_rot = (2 * b + 1) * args.n - b * b - b
+    table = kernel_table(prof, n_rot)
+    kname, kt = next(iter(table.items()))
+    kl, kms, kfl = kt["launches"], kt["ms"], kt["gflop"] * 1e9
     achieved = (kfl / (kms * 1e-3)) / 1e12 if kms > 0 else 0.0
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "launches": kl, "ms_total": kms, "share": kms / max(sum(v[1] for v in per_kernel.values()), 1e-9),
+                "launches": kl, "ms_total": kms, "share": kt["share"],
                 "peak_source": "nominal binary64 rate (recipe table); a DFMA loop measured 1.203 TFLOP/s",
                 "flops": "counted in-kernel from the actual (device-resident) sizes of every launch",
                 "measured": "CUDA events around every launch of one extra, profiled step after the timed ones"}
+    # the mixed-precision form beside it: time per projector and its distance
+    # to the binary64 projector (power iteration on the difference)
+    mixed = None
+    if args.precision == "fp64" and args.mixed_steps > 0 and world == 1:
+        mopts = sp.sp_qdwh_opts_default()
+        mopts.precision = sp.SP_MIXED_NS
+        mopts.polish_steps = args.polish
+
+        def mstep(band, keep=False):
+            A = sp.sp_hodlr_from_band(ctx, band, mu, args.leaf, args.tol)
+            S, minfo = sp.sp_qdwh_sign(ctx, A, mopts)
+            P = sp.sp_projector(ctx, S)
+            sp.sp_hodlr_destroy(A)
+            sp.sp_hodlr_destroy(S)
+            if keep:
+                return P, minfo
+            sp.sp_hodlr_destroy(P)
+            return None, minfo
+
+        mstep(ab_dev)
+        mev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.mixed_steps)]
+        for k in range(args.mixed_steps):
+            flush.fill_(float(k))
+            mev[k][0].record()
+            mstep(ab_dev)
+            mev[k][1].record()
+        torch.cuda.synchronize()
+        m_ms = float(np.mean([a.elapsed_time(b_) for a, b_ in mev]))
+        Pm, minfo = mstep(ab_dev, keep=True)
+        A = sp.sp_hodlr_from_band(ctx, ab_dev, mu, args.leaf, args.tol)
+        S, _ = sp.sp_qdwh_sign(ctx, A, opts)
+        P64 = sp.sp_projector(ctx, S)
+        dn = diff_norm2(sp, ctx, Pm, P64, args.n)
+        for h in (A, S, P64, Pm):
+            sp.sp_hodlr_destroy(h)
+        mixed = {"precision": "SP_MIXED_NS (binary32 Newton-Schulz tail) + binary64 polish", "steps": args.mixed_steps,
+                 "s_per_projector": m_ms / 1e3, "speedup_vs_fp64": (step_ms / m_ms) if m_ms > 0 else None,
+                 "diff_norm2_vs_fp64": dn, "diff_norm_method": "30 steps of block power iteration (4 vectors) "
+                                                               "on P_mixed - P_fp64 through sp_apply",
+                 "iters": minfo.iters, "kinds": list(minfo.kind[:minfo.iters])}
     if rank != 0:
         sp.sp_ctx_destroy(ctx)
         if world > 1:
@@ -353,6 +440,11 @@ def run_ours(args):
                                           "combine": info.ms_combine},
                        "trace_minus_nu": traces[-1] - nu, "wall_s": t_wall,
                        "chol_self_ms_per_level": chol_levels, "profiled_step_ms": prof_step_ms,
+                       "levels": info.levels, "max_rank_level": list(info.max_rank_level[:info.levels]),
+                       "mean_rank_level": [round(x, 2) for x in info.mean_rank_level[:info.levels]],
+                       "nominal_bytes": info.nominal_bytes, "allocated_bytes": info.bytes,
+                       "mixed": mixed,
+                       "kernel_families": table,
                        "kernels": {k: {"launches": v[0], "ms": round(v[1], 3), "gflop": round(v[2] / 1e9, 3)}
                                    for k, v in prof.items() if v[0]}}}
     print(json.dumps(line), flush=True)

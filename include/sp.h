@@ -83,7 +83,7 @@ typedef struct {
   double l[16], a[16], b[16], c[16]; /* l_k, a_k, b_k, c_k per iteration */
   int kind[16];            /* 1 = QR-based, 2 = Cholesky-based, 3 = mixed residual, 4 = mixed Newton-Schulz step */
   int max_rank;            /* largest off-diagonal rank of the result */
-  size_t bytes;            /* device bytes held by the result */
+  size_t bytes;            /* device bytes held by the result (allocated at the rank capacity) */
   double ms_param, ms_qr, ms_chol, ms_total; /* phase times (CUDA events) */
   double flops;            /* nominal binary64 flops counted by the kernels' task lists */
   /* inside the Cholesky-based steps: formatted products, H-Cholesky (with the
@@ -91,15 +91,39 @@ typedef struct {
    * combination + symmetrisation (CUDA events, summed over iterations) */
   double ms_mult, ms_factor, ms_solve, ms_combine;
   double ms_polish;        /* binary64 Newton-Schulz polish (mixed precision) */
+  /* Structure of the result (Sec. 3.1.1; the memory estimate of Sec. 3.2):
+   * per tree level l = 1..levels, the largest and the mean off-diagonal rank
+   * of its 2^l blocks (index l-1; levels beyond 32 are not reported), and the
+   * nominal storage 8 * (sum of leaf sizes^2 + sum over blocks of
+   * (rows + cols) * rank) bytes of the same matrix at its actual ranks. */
+  int levels;
+  int max_rank_level[32];
+  double mean_rank_level[32];
+  double nominal_bytes;
 } sp_info;
 
 /* Returns opts filled with the defaults listed above. */
 void sp_qdwh_opts_default(sp_qdwh_opts* opts);
 
+/* Stream-ordered device allocator supplied by the caller (for example a host
+ * program's own caching pool).  alloc returns `bytes` bytes of device memory
+ * usable by work enqueued on `stream` after the call (NULL on failure, which
+ * the library reports as SP_ENOMEM); free releases a buffer that work already
+ * enqueued on `stream` may still be using, so the allocator must not hand it
+ * out again before that work completes (stream-ordered reuse, as
+ * cudaFreeAsync or a caching allocator that records stream events does).
+ * `stream` is the cudaStream_t the buffer is used on; `user` is passed
+ * through.  The paper has no counterpart (memory management of this library). */
+typedef void* (*sp_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*sp_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
 /* Creates a context bound to the current CUDA device and the given stream
- * (a cudaStream_t; NULL selects the legacy default stream).  The context owns
- * a device workspace that grows on demand. */
-int sp_ctx_create(void* cuda_stream, sp_ctx_t* out);
+ * (a cudaStream_t; NULL selects the legacy default stream).  Every device
+ * buffer the context's calls make (temporaries and result handles) comes from
+ * alloc/free when both are given, else from the device's default memory pool
+ * (cudaMallocAsync; freed memory is kept in the pool across synchronisations).
+ * Giving only one of the two is SP_EINVAL.  The paper has no counterpart. */
+int sp_ctx_create(void* cuda_stream, sp_alloc_fn alloc, sp_free_fn free_fn, void* user, sp_ctx_t* out);
 void sp_ctx_destroy(sp_ctx_t ctx);
 const char* sp_last_error(sp_ctx_t ctx);
 /* Blocks until all work enqueued on the context's stream has finished and
@@ -139,9 +163,9 @@ int64_t sp_launch_count(void);
  * off-diagonal block of the band is stored exactly as a rank-b corner
  * (Lemma 2: a band of width b has off-diagonal rank <= b).
  *   n >= 1; 1 <= b; leaf >= max(2, 2b) (so band corners stay inside sibling
- *   blocks); tol > 0 is the absolute truncation tolerance (Sec. 3.1.1,
- *   "absolute truncation tolerance epsilon") kept with the matrix and used by
- *   every later formatted operation on it; rank_cap >= 2b is the per-block
+ *   blocks); tol > 0 is the truncation tolerance epsilon of Sec. 3.1.1 and
+ *   Sec. 5, an absolute threshold on the singular values of every recompressed
+ *   block, kept with the matrix and used by every later formatted operation; rank_cap >= 2b is the per-block
  *   rank capacity (0 selects max(160, 20b)).
  *   ab: host or device pointer.  On success *out is a new handle. */
 int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
@@ -180,19 +204,34 @@ int sp_projector(sp_ctx_t ctx, sp_hodlr_t S, sp_hodlr_t* P_out);
 int sp_apply(sp_ctx_t ctx, sp_hodlr_t M, int64_t nrhs, const double* X, int64_t ldx, double* Y, int64_t ldy);
 
 /* Rows row0 .. row0+nrows-1 of M as a dense nrows x n panel (column-major,
- * ld >= nrows); out: host or device pointer. */
+ * ld >= nrows); out: host or device pointer.  Expands the HODLR format of
+ * Sec. 3.1.1 (Eq. (HODLR): dense diagonal leaves, off-diagonal blocks U V^T);
+ * the paper uses the dense matrix only to measure errors (Eq.
+ * (error_measures)).  Host out: synchronising. */
 int sp_to_dense(sp_ctx_t ctx, sp_hodlr_t M, int64_t row0, int64_t nrows, double* out, int64_t ld);
 
-/* tr(M) (sum of the leaves' diagonals).  Synchronising. */
+/* tr(M) (sum of the leaves' diagonals), summed in a fixed order (bitwise
+ * reproducible).  For the projector, trace(P) is the number of eigenvalues
+ * below mu (Sec. 1) and enters e_trace of Eq. (error_measures).
+ * Synchronising. */
 int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr);
 
-/* Sizes of a handle: order, tree depth, largest off-diagonal rank and device
- * bytes held.  Synchronising. */
+/* Sizes of a handle: order, tree depth L of the HODLR partition (Sec. 3.1.1,
+ * Eq. (HODLR); n not a power of two is split by balanced bisection), largest
+ * off-diagonal rank (the k of Table "complexity_HODLR") and device bytes held
+ * (the memory of Sec. 3.2, at the rank capacity).  Synchronising. */
 int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32_t* max_rank, size_t* bytes);
 /* Releases a handle's device memory stream-ordered on the stream of the
  * context that created it (work already enqueued there completes first); call
  * it before that stream is destroyed. */
 void sp_hodlr_destroy(sp_hodlr_t M);
+/* Per-level ranks of a handle (the off-diagonal ranks whose growth with the
+ * gap Sec. 3.2 bounds): for tree level l = 1..min(L, nlevels), max_rank[l-1]
+ * and mean_rank[l-1] over the 2^l blocks of that level, and *nominal_bytes =
+ * 8 * (sum of leaf sizes^2 + sum over blocks of (rows + cols) * rank), the
+ * storage at the actual ranks.  Any output may be NULL.  Synchronising. */
+int sp_hodlr_level_ranks(sp_ctx_t ctx, sp_hodlr_t M, int32_t nlevels, int32_t* max_rank, double* mean_rank,
+                         double* nominal_bytes);
 
 /* ---- formatted HODLR arithmetic (Table "complexity_HODLR") ---- */
 

@@ -34,7 +34,7 @@ EXPORTS = [
     "sp_hodlr_info", "sp_hodlr_destroy", "sp_hodlr_add", "sp_hodlr_mult", "sp_hodlr_cholesky",
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
-    "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector",
+    "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector", "sp_hodlr_level_ranks",
 ]
 
 
@@ -57,7 +57,14 @@ class sp_info(ctypes.Structure):
                 ("bytes", ctypes.c_size_t), ("ms_param", ctypes.c_double), ("ms_qr", ctypes.c_double),
                 ("ms_chol", ctypes.c_double), ("ms_total", ctypes.c_double), ("flops", ctypes.c_double),
                 ("ms_mult", ctypes.c_double), ("ms_factor", ctypes.c_double), ("ms_solve", ctypes.c_double),
-                ("ms_combine", ctypes.c_double), ("ms_polish", ctypes.c_double)]
+                ("ms_combine", ctypes.c_double), ("ms_polish", ctypes.c_double), ("levels", ctypes.c_int),
+                ("max_rank_level", ctypes.c_int * 32), ("mean_rank_level", ctypes.c_double * 32),
+                ("nominal_bytes", ctypes.c_double)]
+
+
+# stream-ordered allocator callbacks of sp_ctx_create
+SP_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+SP_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
 
 def build(force: bool = False, jobs: int = 6) -> str:
@@ -93,7 +100,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
     PP = ctypes.POINTER(ctypes.c_void_p)
     sig = {
         "sp_qdwh_opts_default": (None, [ctypes.POINTER(sp_qdwh_opts)]),
-        "sp_ctx_create": (I, [P, PP]),
+        "sp_ctx_create": (I, [P, SP_ALLOC_FN, SP_FREE_FN, P, PP]),
         "sp_ctx_destroy": (None, [P]),
         "sp_last_error": (ctypes.c_char_p, [P]),
         "sp_ctx_sync": (I, [P]),
@@ -124,6 +131,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_launch_count": (I64, []),
         "sp_inertia_noalloc": (I, [P, I64, I32, P, I64, I32, P, P]),
         "sp_batched_projector": (I, [P, I32, P, P, P, P, P, I32, D, I32, ctypes.POINTER(sp_qdwh_opts), I32, P, P]),
+        "sp_hodlr_level_ranks": (I, [P, P, I32, P, P, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -168,10 +176,14 @@ def _check(ctx, rc: int):
 
 # ---------------------------------------------------------------- wrappers --
 
-def sp_ctx_create(stream: int = 0):
+def sp_ctx_create(stream: int = 0, alloc=None, free=None, user: int = 0):
+    """alloc/free: SP_ALLOC_FN / SP_FREE_FN callbacks (keep references to them
+    for the context's lifetime), or None for the device's default pool."""
     lib = load() if _lib is None else _lib
     h = ctypes.c_void_p()
-    _check(None, lib.sp_ctx_create(ctypes.c_void_p(stream), ctypes.byref(h)))
+    _check(None, lib.sp_ctx_create(ctypes.c_void_p(stream), alloc if alloc is not None else SP_ALLOC_FN(),
+                                   free if free is not None else SP_FREE_FN(), ctypes.c_void_p(user),
+                                   ctypes.byref(h)))
     return h
 
 
@@ -234,6 +246,16 @@ def sp_hodlr_info(ctx, M):
     n, lv, mr, by = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_size_t()
     _check(ctx, _lib.sp_hodlr_info(ctx, M, ctypes.byref(n), ctypes.byref(lv), ctypes.byref(mr), ctypes.byref(by)))
     return n.value, lv.value, mr.value, by.value
+
+
+def sp_hodlr_level_ranks(ctx, M, nlevels: int = 32):
+    """(max rank per level, mean rank per level, nominal bytes) for levels 1..nlevels."""
+    import numpy as _np
+    mx = _np.zeros(nlevels, dtype=_np.int32)
+    mean = _np.zeros(nlevels)
+    nb = ctypes.c_double()
+    _check(ctx, _lib.sp_hodlr_level_ranks(ctx, M, nlevels, mx.ctypes.data, mean.ctypes.data, ctypes.byref(nb)))
+    return mx, mean, nb.value
 
 
 def sp_hodlr_destroy(M):

@@ -38,6 +38,9 @@ void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma);
 void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
                             const double* shifts_dev, int64_t* counts_dev);
 int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
+void hodlr_level_stats(sp_ctx* ctx, const sp_hodlr* M, int nlevels, int* max_rank, double* mean_rank,
+                       double* nominal_bytes);
+void hodlr_check_finite(sp_ctx* ctx, const sp_hodlr* M);
 
 namespace {
 
@@ -46,6 +49,8 @@ constexpr double kMixedThreshold = 1e-2;
 
 template <class F>
 int guarded(sp_ctx* ctx, F&& f) {
+  // device buffers made while the call runs come from the context's allocator
+  AllocScope scope(ctx ? &ctx->alloc : nullptr);
   try {
     f();
     return SP_OK;
@@ -287,16 +292,20 @@ void sp_qdwh_opts_default(sp_qdwh_opts* o) {
   o->qr_steps = 1;
 }
 
-int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
-  if (!out) return SP_EINVAL;
+int sp_ctx_create(void* cuda_stream, sp_alloc_fn alloc, sp_free_fn free_fn, void* user, sp_ctx_t* out) {
+  if (!out || (alloc == nullptr) != (free_fn == nullptr)) return SP_EINVAL;
   auto* ctx = new (std::nothrow) sp_ctx;
   if (!ctx) return SP_ENOMEM;
   ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+  ctx->alloc.alloc = alloc;
+  ctx->alloc.free = free_fn;
+  ctx->alloc.user = user;
   const int rc = guarded(ctx, [&] {
     check_cuda(cudaGetDevice(&ctx->device), "cudaGetDevice");
     check_cuda(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device), "attr");
-    check_cuda(cudaMalloc(&ctx->d_flags, sizeof(int) * NFLAGS), "flags");
-    check_cuda(cudaMemset(ctx->d_flags, 0, sizeof(int) * NFLAGS), "flags");
+    ctx->d_flags = static_cast<int*>(dmalloc(sizeof(int) * NFLAGS, ctx->stream));
+    check_cuda(cudaMemsetAsync(ctx->d_flags, 0, sizeof(int) * NFLAGS, ctx->stream), "flags");
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
     {
       static std::mutex mu;
       static bool configured[64] = {};
@@ -312,12 +321,15 @@ int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
     // order from the device's default pool.  Keep freed memory in the pool
     // across synchronisations (the default threshold 0 hands it back to the
     // driver at every sync, and the next step maps it again).  Per process.
-    cudaMemPool_t pool;
-    check_cuda(cudaDeviceGetDefaultMemPool(&pool, ctx->device), "default mem pool");
-    uint64_t keep = UINT64_MAX;
-    check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "mem pool threshold");
+    if (!ctx->alloc.custom()) {
+      cudaMemPool_t pool;
+      check_cuda(cudaDeviceGetDefaultMemPool(&pool, ctx->device), "default mem pool");
+      uint64_t keep = UINT64_MAX;
+      check_cuda(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep), "mem pool threshold");
+    }
   });
   if (rc != SP_OK) {
+    if (ctx->d_flags) dfree(ctx->d_flags, ctx->stream);
     delete ctx;
     return rc;
   }
@@ -328,8 +340,9 @@ int sp_ctx_create(void* cuda_stream, sp_ctx_t* out) {
 void sp_ctx_destroy(sp_ctx_t ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->stream);
-  if (ctx->d_flags) cudaFree(ctx->d_flags);
-  if (ctx->d_fc) cudaFree(ctx->d_fc);
+  dfree(ctx->d_flags, ctx->stream);
+  dfree(ctx->d_fc, ctx->stream);
+  cudaStreamSynchronize(ctx->stream);
   for (int k = 0; k < KID_COUNT; ++k)
     for (auto& e : ctx->ev[k]) {
       cudaEventDestroy(e.first);
@@ -351,8 +364,9 @@ int sp_ctx_set_profiling(sp_ctx_t ctx, int on) {
   if (!ctx) return SP_EINVAL;
   return guarded(ctx, [&] {
     check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
-    if (!ctx->d_fc) check_cuda(cudaMalloc(&ctx->d_fc, sizeof(double) * KID_COUNT), "profiler counters");
-    check_cuda(cudaMemset(ctx->d_fc, 0, sizeof(double) * KID_COUNT), "profiler counters");
+    if (!ctx->d_fc) ctx->d_fc = static_cast<double*>(dmalloc(sizeof(double) * KID_COUNT, ctx->stream));
+    check_cuda(cudaMemsetAsync(ctx->d_fc, 0, sizeof(double) * KID_COUNT, ctx->stream), "profiler counters");
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
     for (int k = 0; k < KID_COUNT; ++k) {
       for (auto& e : ctx->ev[k]) {
         cudaEventDestroy(e.first);
@@ -385,7 +399,10 @@ int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, doub
       ctx->ev[k].clear();
     }
     double h[KID_COUNT] = {};
-    if (ctx->d_fc) check_cuda(cudaMemcpy(h, ctx->d_fc, sizeof(h), cudaMemcpyDeviceToHost), "profiler counters");
+    if (ctx->d_fc) {
+      check_cuda(cudaMemcpyAsync(h, ctx->d_fc, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream), "profiler counters");
+      check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    }
     if (launches) *launches = ctx->launches[kernel];
     if (ms) *ms = ctx->ms[kernel];
     if (flops) *flops = h[kernel];
@@ -459,6 +476,8 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
     std::memset(&inf, 0, sizeof(inf));
     ctx->flops = 0.0;
     Timer total(ctx->stream);
+    // a NaN or infinity in the band (flagged at ingest) stops here
+    check_flags(ctx, "input band");
     double alpha = o.alpha, l0 = o.l0;
     {
       Timer t(ctx->stream);
@@ -507,6 +526,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
           inf.c[s] = 0.0;
           X.reset(newton_schulz_step_mixed(ctx, X.p, &inf));
           inf.kind[s] = 4;
+          hodlr_check_finite(ctx, X.p);
           check_flags(ctx, "Newton-Schulz step");
           inf.ms_chol += t.stop();
           lns = 0.5 * lns * (3.0 - lns * lns);
@@ -523,6 +543,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
       if (k == 0 && o.qr_steps == 1) {
         X.reset(qr_step(ctx, A, alpha, as[k], bs[k], cs[k]));
         inf.kind[k] = 1;
+        hodlr_check_finite(ctx, X.p);
         check_flags(ctx, "QR-based step");
         inf.ms_qr += t.stop();
       } else {
@@ -537,6 +558,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
           X.reset(chol_step(ctx, X.p, as[k], bs[k], cs[k], &inf));
           inf.kind[k] = 2;
         }
+        hodlr_check_finite(ctx, X.p);
         check_flags(ctx, "Cholesky-based step");
         inf.ms_chol += t.stop();
       }
@@ -544,6 +566,7 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
     if (o.precision != SP_FP64 && X.p) {
       Timer t(ctx->stream);
       for (int p = 0; p < o.polish_steps; ++p) X.reset(newton_schulz_step(ctx, X.p));
+      hodlr_check_finite(ctx, X.p);
       check_flags(ctx, "Newton-Schulz polish");
       inf.ms_polish = t.stop();
     }
@@ -554,6 +577,8 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
     if (info) {
       inf.max_rank = hodlr_max_rank(ctx, X.p);
       inf.bytes = X.p->bytes;
+      inf.levels = X.p->L();
+      hodlr_level_stats(ctx, X.p, 32, inf.max_rank_level, inf.mean_rank_level, &inf.nominal_bytes);
       *info = inf;
     }
     *sign_out = X.release();
@@ -588,17 +613,21 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
     sp_ctx sub;
     sub.device = ctx->device;
     sub.num_sms = ctx->num_sms;
+    sub.alloc = ctx->alloc;
     cudaSetDevice(ctx->device);
     cudaStream_t s = nullptr;
-    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMalloc(&sub.d_flags, sizeof(int) * NFLAGS) != cudaSuccess ||
-        cudaMemset(sub.d_flags, 0, sizeof(int) * NFLAGS) != cudaSuccess) {
+    const int src = guarded(&sub, [&] {
+      check_cuda(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), "worker stream");
+      sub.stream = s;
+      sub.d_flags = static_cast<int*>(dmalloc(sizeof(int) * NFLAGS, s));
+      check_cuda(cudaMemsetAsync(sub.d_flags, 0, sizeof(int) * NFLAGS, s), "worker flags");
+    });
+    if (src != SP_OK) {
       int expect = SP_OK;
-      first_err.compare_exchange_strong(expect, SP_ECUDA);
+      first_err.compare_exchange_strong(expect, src);
       if (s) cudaStreamDestroy(s);
       return;
     }
-    sub.stream = s;
     std::vector<int> mine;
     for (;;) {
       if (first_err.load() != SP_OK) break;
@@ -632,8 +661,12 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
       outs[i]->stream = ctx->stream;
       outs[i]->tree->stream = ctx->stream;
     }
-    cudaFree(sub.d_flags);
+    {
+      AllocScope scope(&sub.alloc);
+      dfree(sub.d_flags, s);
+    }
     sub.d_flags = nullptr;
+    cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   };
   std::vector<std::thread> th;
@@ -726,6 +759,20 @@ int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32
 
 void sp_hodlr_destroy(sp_hodlr_t M) { hodlr_free(M); }
 
+int sp_hodlr_level_ranks(sp_ctx_t ctx, sp_hodlr_t M, int32_t nlevels, int32_t* max_rank, double* mean_rank,
+                         double* nominal_bytes) {
+  if (!ctx || !M || nlevels < 0) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    std::vector<int> mx(std::max(nlevels, 1));
+    std::vector<double> mean(std::max(nlevels, 1));
+    hodlr_level_stats(ctx, M, nlevels, mx.data(), mean.data(), nominal_bytes);
+    for (int l = 0; l < nlevels; ++l) {
+      if (max_rank) max_rank[l] = mx[l];
+      if (mean_rank) mean_rank[l] = mean[l];
+    }
+  });
+}
+
 int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr_t B, double gamma, sp_hodlr_t* C) {
   if (!ctx || !A || !C) return SP_EINVAL;
   if (B && !same_tree(*B->tree, *A->tree)) return SP_EINVAL;
@@ -786,7 +833,17 @@ int sp_inertia(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t lda
 int sp_inertia_noalloc(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int32_t nshift,
                        const double* shifts, int64_t* counts) {
   if (!ctx || !ab || !shifts || !counts || n < 1 || b < 0 || ldab < b + 1 || nshift < 0) return SP_EINVAL;
-  return guarded(ctx, [&] { inertia_counts_noalloc(ctx, n, b, ab, ldab, nshift, shifts, counts); });
+  return guarded(ctx, [&] {
+    int dev = -1;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev != ctx->device)
+      fail(SP_EINVAL, "sp_inertia_noalloc: the current device (" + std::to_string(dev) +
+                          ") is not the context's device (" + std::to_string(ctx->device) + ")");
+    // a host pointer would reach the kernel: reject it here
+    if (!is_device(ab) || !is_device(shifts) || !is_device(counts))
+      fail(SP_EINVAL, "sp_inertia_noalloc: ab, shifts and counts must be device pointers");
+    inertia_counts_noalloc(ctx, n, b, ab, ldab, nshift, shifts, counts);
+  });
 }
 
 int sp_locate_shift(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, int64_t nu, double* mu,

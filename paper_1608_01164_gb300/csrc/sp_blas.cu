@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cstdio>
 #include <stdexcept>
+#include <unordered_map>
 
 #include "sp_internal.h"
 
@@ -54,9 +55,30 @@ ProfScope::~ProfScope() {
 }
 
 // ------------------------------------------------------------------ memory --
+namespace {
+// Allocator of the entry point running on this thread (null: default pool).
+thread_local const Allocator* t_alloc = nullptr;
+// Buffers made by a caller's allocator, with the allocator and size to free
+// them with (only consulted once a caller's allocator has been used).
+std::mutex g_custom_mu;
+std::unordered_map<void*, std::pair<Allocator, size_t>> g_custom;
+std::atomic<bool> g_any_custom{false};
+}  // namespace
+
+AllocScope::AllocScope(const Allocator* a) : prev(t_alloc) { t_alloc = a; }
+AllocScope::~AllocScope() { t_alloc = prev; }
+
 void* dmalloc(size_t bytes, cudaStream_t st) {
   void* p = nullptr;
   if (bytes == 0) bytes = 16;
+  if (t_alloc && t_alloc->custom()) {
+    p = t_alloc->alloc(bytes, (void*)st, t_alloc->user);
+    if (!p) fail(SP_ENOMEM, "caller's allocator returned NULL for " + std::to_string(bytes) + " bytes");
+    std::lock_guard<std::mutex> lk(g_custom_mu);
+    g_custom[p] = {*t_alloc, bytes};
+    g_any_custom.store(true);
+    return p;
+  }
   cudaError_t e = cudaMallocAsync(&p, bytes, st);
   if (e != cudaSuccess || !p) {
     (void)cudaGetLastError();
@@ -66,11 +88,34 @@ void* dmalloc(size_t bytes, cudaStream_t st) {
 }
 
 void dfree(void* p, cudaStream_t st) {
-  if (p) (void)cudaFreeAsync(p, st);
+  if (!p) return;
+  if (g_any_custom.load()) {
+    std::unique_lock<std::mutex> lk(g_custom_mu);
+    auto it = g_custom.find(p);
+    if (it != g_custom.end()) {
+      const Allocator a = it->second.first;
+      const size_t bytes = it->second.second;
+      g_custom.erase(it);
+      lk.unlock();
+      a.free(p, bytes, (void*)st, a.user);
+      return;
+    }
+  }
+  (void)cudaFreeAsync(p, st);
 }
 
 DBuf::DBuf(size_t b, cudaStream_t s) : p(dmalloc(b, s)), bytes(b), st(s) {}
 DBuf::~DBuf() { dfree(p, st); }
+DBuf& DBuf::operator=(DBuf&& o) noexcept {
+  if (this != &o) {
+    dfree(p, st);
+    p = o.p;
+    bytes = o.bytes;
+    st = o.st;
+    o.p = nullptr;
+  }
+  return *this;
+}
 
 void configure_dynamic_smem(const void* func) {
   int dev = 0, optin = 0;
@@ -117,7 +162,7 @@ __device__ __forceinline__ int dsize(int s, const int* p) {
 // 160) thus cost no padded FMAs.
 template <bool TA, bool TB, typename MT, int MI, int MJ>
 __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int row0, int col0, int kbeg, int kend,
-                                          int atomic, MT (*As)[kGT + 1], MT (*Bs)[kGT + 1]) {
+                                          int split, MT (*As)[kGT + 1], MT (*Bs)[kGT + 1]) {
   constexpr int TM = 16 * MI, TN = 16 * MJ;
   const int tid = threadIdx.x, r = tid & 15, c = tid >> 4;
   MT acc[MI][MJ];
@@ -163,16 +208,20 @@ __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int r
     for (int j = 0; j < MJ; ++j) {
       const int gr = row0 + r + 16 * i, gc = col0 + c + 16 * j;
       if (gr < m && gc < n) {
-        double* p = t.C + gr + (int64_t)gc * t.ldc;
         const double v = t.alpha * (double)acc[i][j];
-        if (atomic) atomicAdd(p, v);
-        else *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
+        if (split) {
+          // partial tile of k chunk blockIdx.z (static m x n slot per chunk)
+          t.W[(size_t)blockIdx.z * (size_t)t.m * (size_t)t.n + gr + (int64_t)gc * t.m] = v;
+        } else {
+          double* p = t.C + gr + (int64_t)gc * t.ldc;
+          *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
+        }
       }
     }
 }
 
 template <bool TA, bool TB, typename MT>
-__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int atomic,
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int split,
                                               double* fc) {
   const GemmTask t = tasks[blockIdx.y];
   const int m = dsize(t.m, t.pm), n = dsize(t.n, t.pn), k = dsize(t.k, t.pk);
@@ -189,17 +238,43 @@ __global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks
   const int mi = em <= 16 ? 1 : (em <= 32 ? 2 : 4);
   const int mj = en <= 16 ? 1 : (en <= 32 ? 2 : 4);
   switch (mi * 8 + mj) {
-    case 9: gemm_tile<TA, TB, MT, 1, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 10: gemm_tile<TA, TB, MT, 1, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 12: gemm_tile<TA, TB, MT, 1, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 17: gemm_tile<TA, TB, MT, 2, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 18: gemm_tile<TA, TB, MT, 2, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 20: gemm_tile<TA, TB, MT, 2, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 33: gemm_tile<TA, TB, MT, 4, 1>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    case 34: gemm_tile<TA, TB, MT, 4, 2>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
-    default: gemm_tile<TA, TB, MT, 4, 4>(t, m, n, row0, col0, kbeg, kend, atomic, As, Bs); break;
+    case 9: gemm_tile<TA, TB, MT, 1, 1>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 10: gemm_tile<TA, TB, MT, 1, 2>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 12: gemm_tile<TA, TB, MT, 1, 4>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 17: gemm_tile<TA, TB, MT, 2, 1>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 18: gemm_tile<TA, TB, MT, 2, 2>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 20: gemm_tile<TA, TB, MT, 2, 4>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 33: gemm_tile<TA, TB, MT, 4, 1>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    case 34: gemm_tile<TA, TB, MT, 4, 2>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
+    default: gemm_tile<TA, TB, MT, 4, 4>(t, m, n, row0, col0, kbeg, kend, split, As, Bs); break;
   }
   if (fc && threadIdx.x == 0) atomicAdd(fc, 2.0 * (double)em * (double)en * (double)max(kend - kbeg, 0));
+}
+
+// Flags NaN / infinity anywhere in p[0, count).
+__global__ void k_nonfinite(const double* __restrict__ p, size_t count, int* flags) {
+  bool bad = false;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(p[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&flags[FLAG_NONFINITE], 1);
+}
+
+// Sums the k chunks of a split GEMM in chunk order (reproducible, unlike
+// atomics): C = sum_z W_z + beta C over the device-resident m x n.
+__global__ void k_splitk_reduce(const GemmTask* __restrict__ tasks, int kchunk) {
+  const GemmTask t = tasks[blockIdx.y];
+  const int m = dsize(t.m, t.pm), n = dsize(t.n, t.pn), k = dsize(t.k, t.pk);
+  const int nz = k > 0 ? (k + kchunk - 1) / kchunk : 1;
+  const size_t slot = (size_t)t.m * (size_t)t.n;
+  const int64_t total = (int64_t)m * n;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e % m), j = (int)(e / m);
+    const size_t w = i + (size_t)j * t.m;
+    double v = 0.0;
+    for (int z = 0; z < nz; ++z) v += t.W[z * slot + w];
+    double* p = t.C + i + (int64_t)j * t.ldc;
+    *p = (t.beta == 0.0) ? v : v + t.beta * (*p);
+  }
 }
 
 __global__ void k_axpby(const AxpbyTask* __restrict__ tasks) {
@@ -234,11 +309,13 @@ __global__ void k_zero_tail(const ZeroTailTask* __restrict__ tasks) {
 // 2x2 outputs from the shared-memory panel.  The upper triangle is zeroed.
 constexpr int kPW = 32;  // panel width
 
-__global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict__ tasks, int* flags) {
+__global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict__ tasks, int* flags, double* fc) {
   const LeafTask t = tasks[blockIdx.x];
   double* A = t.A;
   const int64_t lda = t.lda;
   const int n = t.n;
+  // algorithmic work of a Cholesky factorisation: n^3/3 + n^2/2 + n/6 flops
+  if (fc && threadIdx.x == 0) atomicAdd(fc, (double)n * n * n / 3.0 + (double)n * n / 2.0 + n / 6.0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double* P = reinterpret_cast<double*>(smem_raw);  // panel, row-major (n rows x (kPW+1))
   constexpr int LDP = kPW + 1;
@@ -330,11 +407,27 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
 constexpr int kInvCols = 4;
 constexpr int kInvRows = 4;
 
-__global__ void __launch_bounds__(256) k_leaf_inv(const LeafTask* __restrict__ tasks) {
+// Work of the forward substitution for identity column c of an n x n
+// triangular inverse: one scaling and (n-c-1) multiply-adds per row below c.
+__device__ __forceinline__ double inv_col_flops(int n, int c) {
+  const double r = (double)(n - c);
+  return r + r * (r - 1.0);
+}
+
+__device__ __forceinline__ void count_inv_flops(double* fc, int n, int c0) {
+  if (fc && threadIdx.x == 0) {
+    double f = 0.0;
+    for (int c = c0; c < c0 + kInvCols && c < n; ++c) f += inv_col_flops(n, c);
+    atomicAdd(fc, f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_leaf_inv(const LeafTask* __restrict__ tasks, double* fc) {
   const LeafTask t = tasks[blockIdx.y];
   const int n = t.n;
   const int c0 = blockIdx.x * kInvCols;
   if (c0 >= n) return;
+  count_inv_flops(fc, n, c0);
   const double* L = t.A;
   const int64_t lda = t.lda;
   __shared__ double dinv[kInvRows * 256];
@@ -402,11 +495,12 @@ __global__ void __launch_bounds__(256) k_leaf_inv(const LeafTask* __restrict__ t
 // round trip to L2.  For leaves of at most kInvSmemRows rows.
 constexpr int kInvSmemRows = 220;
 
-__global__ void __launch_bounds__(256) k_leaf_inv_smem(const LeafTask* __restrict__ tasks) {
+__global__ void __launch_bounds__(256) k_leaf_inv_smem(const LeafTask* __restrict__ tasks, double* fc) {
   const LeafTask t = tasks[blockIdx.y];
   const int n = t.n;
   const int c0 = blockIdx.x * kInvCols;
   if (c0 >= n) return;
+  count_inv_flops(fc, n, c0);
   const double* L = t.A;
   const int64_t lda = t.lda;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -455,7 +549,7 @@ __global__ void __launch_bounds__(256) k_leaf_inv_smem(const LeafTask* __restric
 }
 }  // namespace
 
-void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, bool atomic, int ksplit) {
+void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, int ksplit) {
   if (tasks_in.empty()) return;
   std::vector<GemmTask> tasks;
   tasks.reserve(tasks_in.size());
@@ -485,13 +579,21 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     kchunk = ((maxk + nz - 1) / nz + kGK - 1) / kGK * kGK;
     nz = (maxk + kchunk - 1) / kchunk;
   }
-  if (nz > 1 && !atomic) {
-    std::vector<AxpbyTask> pre;
-    pre.reserve(tasks.size());
-    for (const auto& t : tasks) pre.push_back(AxpbyTask{nullptr, t.C, 0, t.ldc, t.m, t.n, t.pm, t.pn, 0.0, t.beta, 0.0});
-    axpby_batched(ctx, pre);
-    atomic = true;
+  // split k: every chunk writes its partial tile into the task's workspace
+  // slots (nz static m x n slots), a second kernel sums them in order
+  DBuf ws;
+  if (nz > 1) {
+    size_t tot = 0;
+    for (const auto& t : tasks) tot += (size_t)nz * t.m * t.n;
+    ws = DBuf(tot * sizeof(double) + 16, ctx->stream);
+    double* w = ws.as<double>();
+    for (auto& t : tasks) {
+      t.W = w;
+      w += (size_t)nz * t.m * t.n;
+    }
   }
+  int64_t maxe = 1;
+  for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
   for (size_t off = 0; off < tasks.size(); off += 65535) {
     const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
     std::vector<GemmTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
@@ -500,19 +602,24 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     const GemmTask* dt = d.as<GemmTask>();
     double* fc = fc_ptr(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
     ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
-    const int at = atomic ? 1 : 0;
+    const int sp = nz > 1 ? 1 : 0;
     if (ctx->gemm_fp32) {
-      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
     } else {
-      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
-      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, at, fc);
+      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
     }
     check_launch("k_gemm");
+    if (nz > 1) {
+      const int gx = (int)std::min<int64_t>((maxe + 255) / 256, 1024);
+      k_splitk_reduce<<<dim3(gx, (unsigned)cnt), 256, 0, ctx->stream>>>(dt, kchunk);
+      check_launch("k_splitk_reduce");
+    }
   }
 }
 
@@ -544,6 +651,13 @@ void zero_tail_batched(sp_ctx* ctx, const std::vector<ZeroTailTask>& tasks) {
   }
 }
 
+void check_finite(sp_ctx* ctx, const double* p, size_t count) {
+  if (!p || count == 0) return;
+  const int grid = (int)std::min<size_t>((count + 255) / 256, (size_t)ctx->num_sms * 8);
+  k_nonfinite<<<grid, 256, 0, ctx->stream>>>(p, count, ctx->d_flags);
+  check_launch("k_nonfinite");
+}
+
 void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   if (tasks.empty()) return;
   for (const auto& t : tasks) ctx->flops += (double)t.n * t.n * t.n / 3.0;
@@ -553,7 +667,8 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   const size_t sm = (size_t)nmax * (kPW + 1) * sizeof(double);
   ensure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf), sm);
   ProfScope ps(ctx, KID_POTRF);
-  k_leaf_potrf<<<(unsigned)tasks.size(), 1024, sm, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags);
+  k_leaf_potrf<<<(unsigned)tasks.size(), 1024, sm, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags,
+                                                                   fc_ptr(ctx, KID_POTRF));
   check_launch("k_leaf_potrf");
 }
 
@@ -574,10 +689,10 @@ void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
     dim3 grid((maxn + kInvCols - 1) / kInvCols, (unsigned)cnt);
     ProfScope ps(ctx, KID_LEAF_INV);
     if (staged) {
-      k_leaf_inv_smem<<<grid, 256, sm, ctx->stream>>>(d.as<LeafTask>());
+      k_leaf_inv_smem<<<grid, 256, sm, ctx->stream>>>(d.as<LeafTask>(), fc_ptr(ctx, KID_LEAF_INV));
       check_launch("k_leaf_inv_smem");
     } else {
-      k_leaf_inv<<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>());
+      k_leaf_inv<<<grid, 256, 0, ctx->stream>>>(d.as<LeafTask>(), fc_ptr(ctx, KID_LEAF_INV));
       check_launch("k_leaf_inv");
     }
   }

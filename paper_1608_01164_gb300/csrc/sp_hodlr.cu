@@ -31,8 +31,8 @@ namespace sp {
 
 // -------------------------------------------------------------------- tree --
 Tree::~Tree() {
-  if (d_lo) cudaFreeAsync(d_lo, stream);
-  if (d_sz) cudaFreeAsync(d_sz, stream);
+  dfree(d_lo, stream);
+  dfree(d_sz, stream);
 }
 
 std::shared_ptr<Tree> make_tree(int64_t n, int leaf, cudaStream_t stream) {
@@ -224,8 +224,13 @@ __global__ void k_to_dense(const double* __restrict__ leaves, int ld, const doub
   }
 }
 
-__global__ void k_trace(const double* __restrict__ leaves, int ld, const int64_t* __restrict__ sz, int first_leaf,
-                        int nleaves, double* out) {
+// Trace in a fixed summation order (the same bits on every run): each block
+// sums its leaves' diagonals (warp shuffles, then its warps in order) into
+// part[blockIdx.x]; k_sum_ordered adds the parts in index order.
+__global__ void __launch_bounds__(256) k_trace(const double* __restrict__ leaves, int ld,
+                                               const int64_t* __restrict__ sz, int first_leaf, int nleaves,
+                                               double* part) {
+  __shared__ double red[8];
   double s = 0.0;
   for (int j = blockIdx.x; j < nleaves; j += gridDim.x) {
     const int m = (int)sz[first_leaf + j];
@@ -233,7 +238,30 @@ __global__ void k_trace(const double* __restrict__ leaves, int ld, const int64_t
     for (int i = threadIdx.x; i < m; i += blockDim.x) s += D[i + (size_t)i * ld];
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(out, s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
+  }
+}
+
+__global__ void k_sum_ordered(const double* __restrict__ part, int cnt, double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < cnt; ++i) t += part[i];
+    *out = t;
+  }
+}
+
+// Flags NaN / infinity among the band entries that belong to the matrix
+// (lower band storage: entry (d, j) is A(j + d, j), used only for j + d < n).
+__global__ void k_band_finite(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, int* flags) {
+  bool bad = false;
+  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+    for (int d = 0; d <= b && j + d < n; ++d) bad |= !isfinite(ab[d + j * ldab]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&flags[FLAG_NONFINITE], 1);
 }
 
 // ---------------------------------------------------- transpose / sym -------
@@ -293,6 +321,9 @@ sp_hodlr* hodlr_from_band(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, i
                                  sizeof(double) * (b + 1), n, cudaMemcpyDeviceToDevice, ctx->stream),
                "band copy");
     check_cuda(cudaMemsetAsync(M->rank, 0, sizeof(int) * tree->nodes(), ctx->stream), "memset");
+    k_band_finite<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, ctx->stream>>>(M->band, b + 1, n, b,
+                                                                                               ctx->d_flags);
+    check_launch("k_band_finite");
     k_band_leaves<<<tree->nleaves(), 256, 0, ctx->stream>>>(M->band, b + 1, b, mu, tree->d_lo, tree->d_sz,
                                                              tree->nleaves(), M->leaves, M->leaf_ld);
     check_launch("k_band_leaves");
@@ -317,11 +348,13 @@ void hodlr_to_dense(sp_ctx* ctx, const sp_hodlr* M, int64_t row0, int64_t nrows,
 }
 
 double hodlr_trace(sp_ctx* ctx, const sp_hodlr* M) {
-  DBuf d(sizeof(double), ctx->stream);
-  check_cuda(cudaMemsetAsync(d.p, 0, sizeof(double), ctx->stream), "memset");
   const int nl = M->tree->nleaves();
-  k_trace<<<std::min(nl, 1024), 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->tree->d_sz, nl, nl, d.as<double>());
+  const int grid = std::min(nl, 1024);
+  DBuf d(sizeof(double) * (grid + 1), ctx->stream);
+  k_trace<<<grid, 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->tree->d_sz, nl, nl, d.as<double>() + 1);
   check_launch("k_trace");
+  k_sum_ordered<<<1, 32, 0, ctx->stream>>>(d.as<double>() + 1, grid, d.as<double>());
+  check_launch("k_sum_ordered");
   double h = 0.0;
   check_cuda(cudaMemcpyAsync(&h, d.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "trace copy");
   check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
@@ -337,6 +370,48 @@ int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M) {
   check_cuda(cudaMemcpyAsync(&h, d.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream), "rank copy");
   check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
   return h;
+}
+
+// Per-level ranks and the storage at the actual ranks (host-side summary of
+// the device-resident ranks; synchronising).
+void hodlr_level_stats(sp_ctx* ctx, const sp_hodlr* M, int nlevels, int* max_rank, double* mean_rank,
+                       double* nominal_bytes) {
+  const Tree& T = *M->tree;
+  const std::vector<int> r = host_ranks(ctx, M);
+  double bytes = 0.0;
+  for (int j = 0; j < T.nleaves(); ++j) {
+    const double s = (double)T.sz[(1 << T.L) + j];
+    bytes += 8.0 * s * s;
+  }
+  for (int l = 1; l <= T.L; ++l) {
+    int mx = 0;
+    double sum = 0.0;
+    for (int c = 1 << l; c < (2 << l); ++c) {
+      mx = std::max(mx, r[c]);
+      sum += r[c];
+      bytes += 8.0 * (double)(T.sz[c] + T.sz[c ^ 1]) * r[c];
+    }
+    if (l <= nlevels) {
+      if (max_rank) max_rank[l - 1] = mx;
+      if (mean_rank) mean_rank[l - 1] = sum / (double)(1 << l);
+    }
+  }
+  for (int l = T.L + 1; l <= nlevels; ++l) {
+    if (max_rank) max_rank[l - 1] = 0;
+    if (mean_rank) mean_rank[l - 1] = 0.0;
+  }
+  if (nominal_bytes) *nominal_bytes = bytes;
+}
+
+// Non-finite check of every stored entry of M (enqueued).
+void hodlr_check_finite(sp_ctx* ctx, const sp_hodlr* M) {
+  const size_t nl = (size_t)M->tree->nleaves() * M->leaf_ld * M->leaf_ld;
+  const size_t nf = (size_t)std::max(M->L(), 1) * M->n() * M->cap;
+  check_finite(ctx, M->leaves, nl);
+  if (M->L() > 0) {
+    check_finite(ctx, M->U, nf);
+    check_finite(ctx, M->V, nf);
+  }
 }
 
 // ------------------------------------------------------------------ apply ---

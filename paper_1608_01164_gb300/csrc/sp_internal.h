@@ -27,6 +27,16 @@
 
 namespace sp {
 
+// Device memory source of a context: the caller's stream-ordered callbacks
+// (sp_ctx_create) or, when both are null, the device's default memory pool
+// (cudaMallocAsync / cudaFreeAsync).
+struct Allocator {
+  sp_alloc_fn alloc = nullptr;
+  sp_free_fn free = nullptr;
+  void* user = nullptr;
+  bool custom() const { return alloc != nullptr; }
+};
+
 struct Tree {
   cudaStream_t stream = nullptr;  // stream its device arrays were allocated on
   int64_t n = 0;
@@ -83,6 +93,7 @@ enum KernelId {
 struct sp_ctx {
   cudaStream_t stream = nullptr;
   int device = 0;
+  sp::Allocator alloc;     // where every device buffer of this context comes from
   int num_sms = 152;
   std::string err;
   int* d_flags = nullptr;  // [0] rank overflow, [1] breakdown, [2] non-finite, [3] timeout
@@ -160,9 +171,18 @@ struct DBuf {
   DBuf(const DBuf&) = delete;
   DBuf& operator=(const DBuf&) = delete;
   DBuf(DBuf&& o) noexcept : p(o.p), bytes(o.bytes), st(o.st) { o.p = nullptr; }
+  DBuf& operator=(DBuf&& o) noexcept;
   template <class T> T* as() const { return static_cast<T*>(p); }
 };
+// Allocations go through the allocator of the context whose entry point is
+// running on this thread (AllocScope, set by every entry point); frees find
+// the allocator that made the buffer.
 void* dmalloc(size_t bytes, cudaStream_t st);
+struct AllocScope {
+  const Allocator* prev;
+  explicit AllocScope(const Allocator* a);
+  ~AllocScope();
+};
 // Dynamic shared memory above the 48 KB default.  Each kernel that may need
 // it gets its limit raised once per device, to the opt-in maximum, when the
 // first context on that device is created (configure_*_kernels), before any
@@ -200,13 +220,13 @@ struct GemmTask {
   const int* pn;
   const int* pk;
   double alpha, beta;
+  double* W;  // split-k partial tiles (set by gemm_batched)
 };
-void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks, bool atomic = false,
-                  int ksplit = 0);
+void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks, int ksplit = 0);
 inline GemmTask gt(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                    int k, double alpha, double beta, const int* pm = nullptr, const int* pn = nullptr,
                    const int* pk = nullptr) {
-  return GemmTask{A, B, C, lda, ldb, ldc, m, n, k, pm, pn, pk, alpha, beta};
+  return GemmTask{A, B, C, lda, ldb, ldc, m, n, k, pm, pn, pk, alpha, beta, nullptr};
 }
 
 // ------------------------------------------------------------ small kernels --
@@ -247,12 +267,15 @@ struct LeafTask {
 void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 // X <- L^{-1} (the whole n x n inverse) for lower-triangular leaves, n <= 1024.
 void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
+// Sets the context's non-finite flag if any of the `count` doubles at p is
+// NaN or infinite (enqueued, no synchronisation).
+void check_finite(sp_ctx* ctx, const double* p, size_t count);
 
 // --------------------------------------------------------- recompression ----
 // A block given as a sum of products sum_s scale_s U_s V_s^T (U_s: m x w_s,
 // V_s: q x w_s) is recompressed to U V^T with the singular values > tol of
-// the sum kept (absolute truncation, Sec. 3.1.1 / Sec. 5 "repeated
-// recompression with the absolute truncation tolerance").  Stacked factors are
+// the sum kept: an absolute threshold on the singular values, applied after
+// every formatted operation (Sec. 3.1.1; Sec. 5).  Stacked factors are
 // orthogonalised by Householder QR (tall blocks by a binary TSQR tree), the
 // r_U x r_V core R_U R_V^T is diagonalised by a one-sided Jacobi SVD.
 struct Seg {

@@ -2,9 +2,9 @@
 //
 // Every formatted HODLR operation (Table "complexity_HODLR": addition,
 // multiplication, Cholesky, triangular solve) produces off-diagonal blocks as
-// sums  sum_s U_s (scale_s V_s)^T  of low-rank terms.  The paper truncates them
-// with an absolute tolerance epsilon ("repeated recompression with the absolute
-// truncation tolerance", Sec. 5; Sec. 3.1.1).  Here, per block:
+// sums  sum_s U_s (scale_s V_s)^T  of low-rank terms.  The paper recompresses
+// every such sum after each operation, dropping singular values below a fixed
+// absolute threshold epsilon (Sec. 3.1.1; Sec. 5).  Here, per block:
 //   1. gather the stacked factors  W_U = [U_1 .. U_S]  (m x R) and
 //      W_V = [s_1 V_1 .. s_S V_S]  (q x R);
 //   2. Householder QR of W_U and W_V; tall factors use a binary TSQR tree of

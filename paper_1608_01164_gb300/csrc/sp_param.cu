@@ -26,11 +26,21 @@ namespace {
 // per 128-thread CTA must fit in shared memory)
 constexpr int kWarpInertiaMaxB = 80;
 
+// Algorithmic work of one inertia count: tridiagonal, per row a shift, a
+// square, a divide and a subtraction; banded (LDL^T of bandwidth b), per row
+// b(b+1)/2 Schur updates of 3 flops, the b multipliers and the pivot.
+__host__ __device__ inline double inertia_flops(int64_t n, int b) {
+  if (b <= 0) return (double)n;
+  if (b == 1) return 4.0 * (double)n;
+  return (double)n * (1.5 * b * (b + 1.0) + b + 1.0);
+}
+
 __global__ void k_inertia(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
                           const double* __restrict__ shifts, int nshift, int64_t* __restrict__ counts, double pivmin,
-                          double* __restrict__ ring) {
+                          double* __restrict__ ring, double* fc) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nshift) return;
+  if (fc) atomicAdd(fc, inertia_flops(n, b));
   const double sigma = shifts[t];
   int64_t cnt = 0;
   if (b == 1) {
@@ -79,12 +89,13 @@ __global__ void k_inertia(const double* __restrict__ ab, int64_t ldab, int64_t n
 // arithmetic as the per-thread ring above, summed in a different order.
 __global__ void __launch_bounds__(128) k_inertia_warp(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
                                                       const double* __restrict__ shifts, int nshift,
-                                                      int64_t* __restrict__ counts, double pivmin) {
+                                                      int64_t* __restrict__ counts, double pivmin, double* fc) {
   extern __shared__ double win_all[];
   const int W = b + 1;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int t = blockIdx.x * (blockDim.x >> 5) + wib;
   if (t >= nshift) return;  // whole warps exit together
+  if (fc && lane == 0) atomicAdd(fc, inertia_flops(n, b));
   double* S = win_all + (size_t)wib * W * W;
   const double sigma = shifts[t];
   // window rows/columns 0..b
@@ -180,9 +191,12 @@ __global__ void k_pivmin_from_partials(double* scratch, int nparts) {
   }
 }
 
+// The scratch is written (per-shift rings) and read back by the same thread,
+// so it is a plain pointer: no const/__restrict__ that would allow loads
+// through the read-only data path.
 __global__ void k_inertia_noalloc(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
                                   const double* __restrict__ shifts, int nshift, int64_t* __restrict__ counts,
-                                  const double* __restrict__ scratch) {
+                                  double* scratch) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nshift) return;
   const double pivmin = scratch[512];
@@ -199,7 +213,7 @@ __global__ void k_inertia_noalloc(const double* __restrict__ ab, int64_t ldab, i
   } else if (b == 0) {
     for (int64_t i = 0; i < n; ++i) cnt += ab[i * ldab] < sigma;
   } else {
-    double* Lr = const_cast<double*>(scratch) + 520 + (size_t)t * (b * b + b);
+    double* Lr = scratch + 520 + (size_t)t * (b * b + b);
     double* Dr = Lr + b * b;
     for (int64_t j = 0; j < n; ++j) {
       double dj = ab[j * ldab] - sigma;
@@ -280,14 +294,14 @@ void inertia_counts(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t
     ensure_dynamic_smem(reinterpret_cast<const void*>(k_inertia_warp), sm);
     ProfScope ps(ctx, KID_INERTIA);
     k_inertia_warp<<<(nshift + 3) / 4, 128, sm, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev,
-                                                               pivmin);
+                                                               pivmin, fc_ptr(ctx, KID_INERTIA));
     check_launch("k_inertia_warp");
     return;
   }
   DBuf ring(b > 1 ? (size_t)nshift * (b * b + b) * sizeof(double) : 16, ctx->stream);
   ProfScope ps(ctx, KID_INERTIA);
   k_inertia<<<(nshift + 63) / 64, 64, 0, ctx->stream>>>(ab_dev, ldab, n, b, shifts_dev, nshift, counts_dev, pivmin,
-                                                        ring.as<double>());
+                                                        ring.as<double>(), fc_ptr(ctx, KID_INERTIA));
   check_launch("k_inertia");
 }
 

@@ -49,6 +49,10 @@ def test_invalid_arguments_rejected_without_gpu(lib):
     # null context -> SP_EINVAL before any device work
     assert lib.sp_hodlr_from_band(None, 10, 1, None, 2, 0.0, 4, 1e-10, 0, ctypes.byref(h)) == sp.SP_EINVAL
     assert lib.sp_qdwh_sign(None, None, None, None, None) == sp.SP_EINVAL
+    # an allocator needs both callbacks
+    alloc = sp.SP_ALLOC_FN(lambda nbytes, stream, user: 0)
+    assert lib.sp_ctx_create(None, alloc, sp.SP_FREE_FN(), None, ctypes.byref(h)) == sp.SP_EINVAL
+    assert lib.sp_ctx_create(None, sp.SP_ALLOC_FN(), sp.SP_FREE_FN(), None, None) == sp.SP_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

@@ -35,10 +35,10 @@ def band_matvec(ab, X):
     return Y
 
 
-def check_invariants(ctx, ab, nu, leaf, precision=None, nprobe=6, tol=1e-8):
+def check_invariants(ctx, ab, nu, leaf, precision=None, nprobe=6, tol=1e-8, trunc=1e-10):
     n = ab.shape[0]
     mu, _, _ = sp.sp_locate_shift(ctx, ab, nu)
-    A = sp.sp_hodlr_from_band(ctx, ab, mu, leaf, 1e-10)
+    A = sp.sp_hodlr_from_band(ctx, ab, mu, leaf, trunc)
     opts = sp.sp_qdwh_opts_default()
     if precision is not None:
         opts.precision = precision
@@ -88,10 +88,85 @@ def test_band8_16384(ctx):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed_ns"])
 def test_tridiagonal_1e5(ctx, precision):
-    """n = 1e5, relative gap ~1e-5: the truncation errors (tol 1e-10 per block)
-    reach the projector as ~2e-8, which the commutation probe sees; the bound
-    is 1e-7 here (1e-8 is the bar where the oracle reaches)."""
+    """n = 1e5, relative gap ~1e-5, at truncation tolerance 1e-12: the 1e-8 bar.
+    (Per the paper's accuracy-versus-epsilon example, the projector's error
+    grows with the truncation tolerance; at the workload's stated 1e-10 it is
+    measured by the next test.)"""
     (_, ab, nu), = sp_inputs.workload(4, n=100000)
     prec = sp.SP_FP64 if precision == "fp64" else sp.SP_MIXED_NS
-    info, idem, comm = check_invariants(ctx, ab, nu, 256, prec, tol=1e-7)
-    print(f"tridiagonal n=1e5 {precision}: iters {info.iters} idem {idem:.1e} comm {comm:.1e}")
+    info, idem, comm = check_invariants(ctx, ab, nu, 256, prec, tol=1e-8, trunc=1e-12)
+    print(f"tridiagonal n=1e5 tol 1e-12 {precision}: iters {info.iters} max rank {info.max_rank} "
+          f"idem {idem:.1e} comm {comm:.1e}")
+
+
+def test_tridiagonal_1e5_at_tol_1e10(ctx):
+    """The same matrix at the workload's stated truncation tolerance 1e-10:
+    the truncation error amplified by the iteration (~4e-8 measured by the
+    commutation probe) sits above 1e-8, so this records its level; the 1e-8
+    bar is the tol 1e-12 run above."""
+    (_, ab, nu), = sp_inputs.workload(4, n=100000)
+    info, idem, comm = check_invariants(ctx, ab, nu, 256, sp.SP_FP64, tol=1e-7, trunc=1e-10)
+    print(f"tridiagonal n=1e5 tol 1e-10: iters {info.iters} max rank {info.max_rank} idem {idem:.1e} comm {comm:.1e}")
+
+
+def test_band4_1e5(ctx):
+    """Paper-scale banded workload: b = 4, N(0,1) entries, n = 1e5, nu = n/2."""
+    (_, ab, nu), = sp_inputs.workload(4, variant="band4", n=100000)
+    info, idem, comm = check_invariants(ctx, ab, nu, 256, tol=1e-8, trunc=1e-12)
+    print(f"b=4 n=1e5 tol 1e-12: iters {info.iters} max rank {info.max_rank} idem {idem:.1e} comm {comm:.1e}")
+
+
+def test_band16_32768(ctx):
+    """Mixed-precision workload's matrix in binary64: b = 16, N(0,1)/4, n = 32768."""
+    ab = sp_inputs.normal_band(32768, 16, sp_inputs.workload_seed(2, 0), 0.25)
+    info, idem, comm = check_invariants(ctx, ab, 16384, 128, tol=1e-8)
+    print(f"b=16 n=32768: iters {info.iters} max rank {info.max_rank} idem {idem:.1e} comm {comm:.1e}")
+
+
+def projector(ctx, ab, nu, leaf, trunc, precision):
+    mu, _, _ = sp.sp_locate_shift(ctx, ab, nu)
+    A = sp.sp_hodlr_from_band(ctx, ab, mu, leaf, trunc)
+    opts = sp.sp_qdwh_opts_default()
+    opts.precision = precision
+    S, info = sp.sp_qdwh_sign(ctx, A, opts)
+    P = sp.sp_projector(ctx, S)
+    sp.sp_hodlr_destroy(A)
+    sp.sp_hodlr_destroy(S)
+    return P, info
+
+
+def diff_norm2(ctx, P1, P2, n, steps=30, s=4, seed=99):
+    """||P1 - P2||_2 by block power iteration on the symmetric difference
+    (a lower bound that converges to the norm), through sp_apply."""
+    X = np.asfortranarray(sp_inputs.normal(seed, n * s).reshape(s, n).T)
+    est = 0.0
+    for _ in range(steps):
+        X, _ = np.linalg.qr(X)
+        X = np.asfortranarray(X)
+        Y1 = np.zeros_like(X, order="F")
+        Y2 = np.zeros_like(X, order="F")
+        sp.sp_apply(ctx, P1, s, X, n, Y1, n)
+        sp.sp_apply(ctx, P2, s, X, n, Y2, n)
+        X = Y1 - Y2
+        est = max(est, float(np.max(np.linalg.norm(X, axis=0))))
+    return est
+
+
+@pytest.mark.parametrize("workload", ["tridiag", "band4"])
+def test_mixed_vs_fp64_1e5(ctx, workload):
+    """The mixed-precision forms against the binary64 form at n = 1e5:
+    ||P_mixed - P_fp64||_2 <= 1e-8 (power iteration on the difference)."""
+    (_, ab, nu), = sp_inputs.workload(4, variant="main" if workload == "tridiag" else "band4", n=100000)
+    n = ab.shape[0]
+    P64, _ = projector(ctx, ab, nu, 256, 1e-10, sp.SP_FP64)
+    try:
+        for prec in (sp.SP_MIXED_FP32, sp.SP_MIXED_NS):
+            Pm, info = projector(ctx, ab, nu, 256, 1e-10, prec)
+            try:
+                d = diff_norm2(ctx, Pm, P64, n)
+                print(f"{workload} n=1e5 precision {prec}: ||P_mixed - P_fp64||_2 ~ {d:.2e} ({info.iters} iters)")
+                assert d <= 1e-8, d
+            finally:
+                sp.sp_hodlr_destroy(Pm)
+    finally:
+        sp.sp_hodlr_destroy(P64)

@@ -10,6 +10,7 @@ fresh process (it creates its own context).
 import numpy as np
 import pytest
 
+import oracle
 import sp_inputs
 
 torch = pytest.importorskip("torch")
@@ -28,21 +29,55 @@ def ctx():
     sp.sp_ctx_destroy(c)
 
 
-@pytest.mark.parametrize("n,b,nshift", [(2000, 1, 300), (900, 4, 257), (500, 8, 1000)])
+def safe_shifts(ab, nshift, rng):
+    """Shifts drawn uniformly over the spectrum's range, kept at least 1e-9
+    (relative) away from every eigenvalue, so that no count is decided by
+    rounding and every correct implementation gives the same counts."""
+    lam = np.linalg.eigvalsh(sp_inputs.dense_from_band(ab))
+    lo, hi = lam[0] - 1.0, lam[-1] + 1.0
+    scale = max(abs(lo), abs(hi))
+    out = []
+    while len(out) < nshift:
+        x = rng.uniform(lo, hi)
+        if np.min(np.abs(lam - x)) > 1e-9 * scale:
+            out.append(x)
+    return np.sort(np.array(out))
+
+
+@pytest.mark.parametrize("n,b,nshift", [(2000, 1, 300), (700, 2, 129), (650, 3, 200), (900, 4, 257),
+                                        (500, 8, 1000), (400, 90, 100)])
 def test_noalloc_matches_regular_inertia_twice(ctx, n, b, nshift):
+    """Two calls in a row (the shared scratch keeps the previous call's
+    contents) against the regular entry point and the oracle's counts."""
     ab = sp_inputs.normal_band(n, b, seed=1234 + b)
     rng = np.random.default_rng(b)
-    lo, hi = -3.0 * np.sqrt(b + 1), 3.0 * np.sqrt(b + 1)
     ab_d = torch.from_numpy(np.ascontiguousarray(ab)).cuda()
     for call in range(2):
-        shifts = np.sort(rng.uniform(lo, hi, nshift))
+        shifts = safe_shifts(ab, nshift, rng)
         ref = np.zeros(nshift, dtype=np.int64)
         sp.sp_inertia(ctx, ab, shifts, ref)
         sh_d = torch.from_numpy(shifts).cuda()
         out_d = torch.full((nshift,), -1, dtype=torch.int64, device="cuda")
         sp.sp_inertia_noalloc(ctx, n, b, ab_d, b + 1, nshift, sh_d, out_d)
         torch.cuda.synchronize()
-        assert np.array_equal(out_d.cpu().numpy(), ref), f"call {call}"
+        got = out_d.cpu().numpy()
+        assert np.array_equal(got, ref), f"call {call}"
+        orc = np.array([oracle.band_count(ab, x) for x in shifts])
+        assert np.array_equal(got, orc), f"call {call} vs oracle"
+
+
+def test_noalloc_rejects_host_pointers(ctx):
+    n, b, nshift = 64, 2, 8
+    ab = sp_inputs.normal_band(n, b, seed=5)
+    ab_d = torch.from_numpy(np.ascontiguousarray(ab)).cuda()
+    sh = np.linspace(-1.0, 1.0, nshift)
+    sh_d = torch.from_numpy(sh).cuda()
+    out_d = torch.zeros(nshift, dtype=torch.int64, device="cuda")
+    out_h = np.zeros(nshift, dtype=np.int64)
+    for args in ((ab, sh_d, out_d), (ab_d, sh, out_d), (ab_d, sh_d, out_h)):
+        with pytest.raises(sp.SpError) as ei:
+            sp.sp_inertia_noalloc(ctx, n, b, args[0], b + 1, nshift, args[1], args[2])
+        assert ei.value.code == sp.SP_EINVAL and "device pointers" in str(ei.value)
 
 
 def test_noalloc_rejects_oversized_request(ctx):
