@@ -216,6 +216,14 @@ int sp_to_dense(sp_ctx_t ctx, sp_hodlr_t M, int64_t row0, int64_t nrows, double*
  * Synchronising. */
 int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr);
 
+/* trace(M A) for a symmetric band A of M's order (lower band storage, ldab >=
+ * b+1; ab host or device): sum_i M(i,i) a_ii + sum_{d=1..b} (M(i+d,i) +
+ * M(i,i+d)) a_{i+d,i}, summed in a fixed order.  With M the projector
+ * Pi_{<mu}(A) of the same A this is the sum of the eigenvalues below mu, the
+ * band energy of the density-matrix application that motivates the paper
+ * (Sec. 1).  Synchronising. */
+int sp_trace_product_band(sp_ctx_t ctx, sp_hodlr_t M, int32_t b, const double* ab, int64_t ldab, double* out);
+
 /* Sizes of a handle: order, tree depth L of the HODLR partition (Sec. 3.1.1,
  * Eq. (HODLR); n not a power of two is split by balanced bisection), largest
  * off-diagonal rank (the k of Table "complexity_HODLR") and device bytes held

@@ -35,6 +35,7 @@ EXPORTS = [
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
     "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector", "sp_hodlr_level_ranks",
+    "sp_trace_product_band",
 ]
 
 
@@ -132,6 +133,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_inertia_noalloc": (I, [P, I64, I32, P, I64, I32, P, P]),
         "sp_batched_projector": (I, [P, I32, P, P, P, P, P, I32, D, I32, ctypes.POINTER(sp_qdwh_opts), I32, P, P]),
         "sp_hodlr_level_ranks": (I, [P, P, I32, P, P, ctypes.POINTER(D)]),
+        "sp_trace_product_band": (I, [P, P, I32, P, I64, ctypes.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -239,6 +241,16 @@ def sp_to_dense(ctx, M, row0: int, nrows: int, out, ld: int):
 def sp_trace(ctx, M) -> float:
     t = ctypes.c_double()
     _check(ctx, _lib.sp_trace(ctx, M, ctypes.byref(t)))
+    return t.value
+
+
+def sp_trace_product_band(ctx, M, ab, b=None, ldab=None) -> float:
+    """trace(M A) for the symmetric band A given as (n, b+1) band storage."""
+    if b is None:
+        b = ab.shape[1] - 1
+        ldab = ab.shape[1]
+    t = ctypes.c_double()
+    _check(ctx, _lib.sp_trace_product_band(ctx, M, b, _ptr(ab), ldab, ctypes.byref(t)))
     return t.value
 
 

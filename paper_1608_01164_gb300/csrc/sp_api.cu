@@ -41,6 +41,7 @@ int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
 void hodlr_level_stats(sp_ctx* ctx, const sp_hodlr* M, int nlevels, int* max_rank, double* mean_rank,
                        double* nominal_bytes);
 void hodlr_check_finite(sp_ctx* ctx, const sp_hodlr* M);
+double hodlr_trace_band(sp_ctx* ctx, const sp_hodlr* M, int b, const double* ab_dev, int64_t ldab);
 
 namespace {
 
@@ -745,6 +746,14 @@ int sp_to_dense(sp_ctx_t ctx, sp_hodlr_t M, int64_t row0, int64_t nrows, double*
 int sp_trace(sp_ctx_t ctx, sp_hodlr_t M, double* tr) {
   if (!ctx || !M || !tr) return SP_EINVAL;
   return guarded(ctx, [&] { *tr = hodlr_trace(ctx, M); });
+}
+
+int sp_trace_product_band(sp_ctx_t ctx, sp_hodlr_t M, int32_t b, const double* ab, int64_t ldab, double* out) {
+  if (!ctx || !M || !ab || !out || b < 0 || ldab < b + 1) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, M->n(), b, ab, ldab);
+    *out = hodlr_trace_band(ctx, M, b, d.as<double>(), b + 1);
+  });
 }
 
 int sp_hodlr_info(sp_ctx_t ctx, sp_hodlr_t M, int64_t* n, int32_t* levels, int32_t* max_rank, size_t* bytes) {

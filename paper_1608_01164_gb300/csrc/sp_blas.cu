@@ -7,6 +7,8 @@
 // while HBM delivers ~6.8 TB/s, so every binary64 kernel here is bound by the
 // FP64 pipe (ridge ~0.18 flop/byte); the tiling aims at keeping each SM's
 // DFMA pipe busy, not at saving bytes.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -397,6 +399,150 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
   }
 }
 
+// ------------------------------------------- leaf Cholesky on a cluster ----
+// Blocked right-looking Cholesky (16 x 16 blocks) of one leaf by a cluster of
+// kCC CTAs on kCC SMs.  Binary64 runs at about two FMAs per clock per SM on
+// this part, so a single SM needs ~0.3 ms for a 195-row leaf, and the leaf
+// factorisations form the H-Cholesky's sequential critical path.  Block step p:
+//  (a) CTA p % kCC factors the diagonal block with one warp (row i of the
+//      block in lane i's registers, one reciprocal square root per column)
+//      and forms the block's inverse in its shared memory;
+//  (b) cluster barrier; the row blocks below are dealt over the cluster and
+//      each becomes L_ip = A_ip L_pp^{-T}, reading L_pp^{-1} from the owner's
+//      shared memory (distributed shared memory);
+//  (c) cluster barrier; the trailing blocks A_ij -= L_ip L_jp^T (p < j <= i)
+//      are dealt round-robin over the cluster;
+//  (d) cluster barrier.
+// The leaf stays in global memory (resident in L2); the cluster barriers
+// (release/acquire at cluster scope) order the CTAs' writes.  The strict
+// upper triangle is zeroed at the end.  A non-positive pivot sets the
+// breakdown flag and continues with pivot 1, as k_leaf_potrf does.
+constexpr int kCB = 16;              // block edge
+constexpr int kCC = 8;               // CTAs per cluster (portable cluster size)
+constexpr int kCMaxN = kCB * 16;     // largest leaf handled (16 block rows)
+
+// Factor the pb x pb diagonal block at D (lower triangle; pb <= kCB) in place
+// and write its inverse to Linv (row-major, zero above the diagonal).  Called
+// by one full warp; lanes 16..31 mirror lanes 0..15 and write nothing.
+__device__ __noinline__ void cluster_diag_block(double* D, int64_t lda, int pb, double (*Linv)[kCB + 1], int* flags) {
+  const unsigned full = 0xffffffffu;
+  const int i = threadIdx.x & 15;
+  const bool writer = (threadIdx.x & 31) < 16;
+  double row[kCB];
+#pragma unroll
+  for (int k = 0; k < kCB; ++k) row[k] = (i < pb && k <= i) ? D[i + (int64_t)k * lda] : (k == i ? 1.0 : 0.0);
+  double yi = 1.0;  // 1 / L_ii of this lane's row
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < kCB; ++j) {
+    double d = __shfl_sync(full, row[j], j);  // pivot: lane j's diagonal entry
+    if (!(d > 0.0)) {
+      bad = true;
+      d = 1.0;
+    }
+    const double yj = rsqrt(d);
+    if (i > j) {
+      row[j] *= yj;
+    } else if (i == j) {
+      row[j] = d * yj;
+      yi = yj;
+    }
+#pragma unroll
+    for (int k = j + 1; k < kCB; ++k) {
+      const double lkj = __shfl_sync(full, row[j], k);
+      if (i > j && k <= i) row[k] = fma(-row[j], lkj, row[k]);
+    }
+  }
+  if (bad && threadIdx.x == 0) atomicOr(&flags[FLAG_BREAKDOWN], 1);
+  // inverse by columns of the substitution: s_i[j] = sum_{k<i} L_ik X_kj,
+  // row k of X final once every k' < k has been added (X_kk = 1/L_kk)
+  double x[kCB];
+#pragma unroll
+  for (int j = 0; j < kCB; ++j) x[j] = 0.0;
+#pragma unroll
+  for (int k = 0; k < kCB; ++k) {
+    if (i == k) {
+#pragma unroll
+      for (int j = 0; j < k; ++j) x[j] = -yi * x[j];
+      x[k] = yi;
+    }
+#pragma unroll
+    for (int j = 0; j <= k; ++j) {
+      const double xkj = __shfl_sync(full, x[j], k);
+      if (i > k) x[j] = fma(row[k], xkj, x[j]);
+    }
+  }
+  if (writer) {
+#pragma unroll
+    for (int k = 0; k < kCB; ++k) {
+      Linv[i][k] = (k <= i) ? x[k] : 0.0;
+      if (i < pb && k <= i) D[i + (int64_t)k * lda] = row[k];
+    }
+  }
+}
+
+__global__ void __cluster_dims__(kCC, 1, 1) __launch_bounds__(256)
+    k_leaf_potrf_cluster(const LeafTask* __restrict__ tasks, int* flags, double* fc) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const LeafTask t = tasks[blockIdx.y];
+  double* A = t.A;
+  const int64_t lda = t.lda;
+  const int n = t.n;
+  const int NB = (n + kCB - 1) / kCB;
+  __shared__ double Linv[kCB][kCB + 1];
+  __shared__ double Bi[kCB][kCB + 1];
+  __shared__ double Bj[kCB][kCB + 1];
+  const int tid = threadIdx.x;
+  const int r = tid & 15, c = tid >> 4;  // 256 threads = one 16 x 16 block
+  if (fc && rank == 0 && tid == 0) atomicAdd(fc, (double)n * n * n / 3.0 + (double)n * n / 2.0 + n / 6.0);
+  for (int p = 0; p < NB; ++p) {
+    const int p0 = p * kCB;
+    const int pb = min(kCB, n - p0);
+    const int owner = p % kCC;
+    if (rank == owner && tid < 32) cluster_diag_block(A + p0 + (int64_t)p0 * lda, lda, pb, Linv, flags);
+    cl.sync();
+    // (b) L_ip = A_ip L_pp^{-T}
+    const double* Lo = cl.map_shared_rank(&Linv[0][0], owner);
+    for (int i = p + 1 + rank; i < NB; i += kCC) {
+      const int i0 = i * kCB, ib = min(kCB, n - i0);
+      Bi[r][c] = (r < ib && c < pb) ? A[(i0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
+      __syncthreads();
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCB; ++k) acc = fma(Bi[r][k], Lo[c * (kCB + 1) + k], acc);
+      if (r < ib && c < pb) A[(i0 + r) + (int64_t)(p0 + c) * lda] = acc;
+      __syncthreads();
+    }
+    cl.sync();
+    // (c) trailing update of the blocks (i, j), p < j <= i < NB
+    const int m = NB - 1 - p;
+    const int nblk = m * (m + 1) / 2;
+    for (int q = rank; q < nblk; q += kCC) {
+      int ii = 0;
+      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
+      const int jj = q - ii * (ii + 1) / 2;
+      const int i = p + 1 + ii, j = p + 1 + jj;
+      const int i0 = i * kCB, ib = min(kCB, n - i0);
+      const int j0 = j * kCB, jb = min(kCB, n - j0);
+      Bi[r][c] = (r < ib && c < pb) ? A[(i0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
+      Bj[r][c] = (r < jb && c < pb) ? A[(j0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
+      __syncthreads();
+      double acc = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCB; ++k) acc = fma(Bi[r][k], Bj[c][k], acc);
+      if (r < ib && c < jb && (i != j || r >= c)) A[(i0 + r) + (int64_t)(j0 + c) * lda] -= acc;
+      __syncthreads();
+    }
+    cl.sync();
+  }
+  for (int64_t e = (int64_t)rank * blockDim.x + tid; e < (int64_t)n * n; e += (int64_t)kCC * blockDim.x) {
+    const int i = (int)(e % n), j = (int)(e / n);
+    if (i < j) A[i + (int64_t)j * lda] = 0.0;
+  }
+}
+
 // Li = L^{-1} for a lower-triangular leaf L (n <= kInvRows * 256).  CTA =
 // (block of kInvCols identity columns, task); forward substitution L X = I
 // restricted to those columns, which are zero above their first column c0,
@@ -664,6 +810,13 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   DBuf d = upload(tasks, ctx->stream);
   int nmax = 1;
   for (const auto& t : tasks) nmax = std::max(nmax, t.n);
+  if (nmax <= kCMaxN) {
+    ProfScope ps(ctx, KID_POTRF);
+    k_leaf_potrf_cluster<<<dim3(kCC, (unsigned)tasks.size()), 256, 0, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags,
+                                                                                     fc_ptr(ctx, KID_POTRF));
+    check_launch("k_leaf_potrf_cluster");
+    return;
+  }
   const size_t sm = (size_t)nmax * (kPW + 1) * sizeof(double);
   ensure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf), sm);
   ProfScope ps(ctx, KID_POTRF);

@@ -193,34 +193,66 @@ __device__ __forceinline__ int leaf_of(const int64_t* lo, int first_leaf, int nl
   return a;
 }
 
+// Entry M(i, j) of a HODLR matrix: a leaf entry, or row i of U times row j
+// of V of the block that holds (i, j) (found from the lowest common ancestor
+// of the two leaves).
+__device__ __forceinline__ double hodlr_entry(const double* __restrict__ leaves, int ld, const double* __restrict__ U,
+                                              const double* __restrict__ V, const int* __restrict__ rank,
+                                              const int64_t* __restrict__ lo, int L, int64_t n, int cap, int64_t i,
+                                              int64_t j) {
+  const int first_leaf = 1 << L;
+  const int li = leaf_of(lo, first_leaf, first_leaf, i), lj = leaf_of(lo, first_leaf, first_leaf, j);
+  if (li == lj) return leaves[(size_t)li * ld * ld + (i - lo[first_leaf + li]) + (size_t)(j - lo[first_leaf + li]) * ld];
+  int x = first_leaf + li, y = first_leaf + lj, d = 0;
+  while (x != y) {
+    x >>= 1;
+    y >>= 1;
+    ++d;
+  }
+  const int ci = (first_leaf + li) >> (d - 1);
+  const int lev = L - d + 1;
+  const int r = rank[ci];
+  const double* Ul = U + (size_t)(lev - 1) * n * cap;
+  const double* Vl = V + (size_t)(lev - 1) * n * cap;
+  double v = 0.0;
+  for (int t = 0; t < r; ++t) v += Ul[i + (size_t)t * n] * Vl[j + (size_t)t * n];
+  return v;
+}
+
 __global__ void k_to_dense(const double* __restrict__ leaves, int ld, const double* __restrict__ U,
                            const double* __restrict__ V, const int* __restrict__ rank, const int64_t* __restrict__ lo,
                            int L, int64_t n, int cap, int64_t row0, int64_t nrows, double* out, int64_t ldo) {
-  const int first_leaf = 1 << L;
   const int64_t total = nrows * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t ri = e % nrows, j = e / nrows;
-    const int64_t i = row0 + ri;
-    const int li = leaf_of(lo, first_leaf, first_leaf, i), lj = leaf_of(lo, first_leaf, first_leaf, j);
-    double v;
-    if (li == lj) {
-      v = leaves[(size_t)li * ld * ld + (i - lo[first_leaf + li]) + (size_t)(j - lo[first_leaf + li]) * ld];
-    } else {
-      int x = first_leaf + li, y = first_leaf + lj, d = 0;
-      while (x != y) {
-        x >>= 1;
-        y >>= 1;
-        ++d;
-      }
-      const int ci = (first_leaf + li) >> (d - 1);
-      const int lev = L - d + 1;
-      const int r = rank[ci];
-      const double* Ul = U + (size_t)(lev - 1) * n * cap;
-      const double* Vl = V + (size_t)(lev - 1) * n * cap;
-      v = 0.0;
-      for (int t = 0; t < r; ++t) v += Ul[i + (size_t)t * n] * Vl[j + (size_t)t * n];
-    }
-    out[ri + j * ldo] = v;
+    out[ri + j * ldo] = hodlr_entry(leaves, ld, U, V, rank, lo, L, n, cap, row0 + ri, j);
+  }
+}
+
+// trace(M A) for a symmetric band A (lower band storage): row i contributes
+// M(i,i) a_ii + sum_{d=1..b} (M(i+d,i) + M(i,i+d)) a_{i+d,i}.  Per-block
+// partial sums in a fixed order (k_sum_ordered adds them).
+__global__ void __launch_bounds__(256) k_trace_band(const double* __restrict__ leaves, int ld,
+                                                    const double* __restrict__ U, const double* __restrict__ V,
+                                                    const int* __restrict__ rank, const int64_t* __restrict__ lo, int L,
+                                                    int64_t n, int cap, const double* __restrict__ ab, int64_t ldab,
+                                                    int b, double* part) {
+  __shared__ double red[8];
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    s += hodlr_entry(leaves, ld, U, V, rank, lo, L, n, cap, i, i) * ab[i * ldab];
+    for (int d = 1; d <= b && i + d < n; ++d)
+      s += (hodlr_entry(leaves, ld, U, V, rank, lo, L, n, cap, i + d, i) +
+            hodlr_entry(leaves, ld, U, V, rank, lo, L, n, cap, i, i + d)) *
+           ab[d + i * ldab];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    part[blockIdx.x] = t;
   }
 }
 
@@ -353,6 +385,20 @@ double hodlr_trace(sp_ctx* ctx, const sp_hodlr* M) {
   DBuf d(sizeof(double) * (grid + 1), ctx->stream);
   k_trace<<<grid, 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->tree->d_sz, nl, nl, d.as<double>() + 1);
   check_launch("k_trace");
+  k_sum_ordered<<<1, 32, 0, ctx->stream>>>(d.as<double>() + 1, grid, d.as<double>());
+  check_launch("k_sum_ordered");
+  double h = 0.0;
+  check_cuda(cudaMemcpyAsync(&h, d.p, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream), "trace copy");
+  check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+  return h;
+}
+
+double hodlr_trace_band(sp_ctx* ctx, const sp_hodlr* M, int b, const double* ab_dev, int64_t ldab) {
+  const int grid = (int)std::min<int64_t>((M->n() + 255) / 256, 1024);
+  DBuf d(sizeof(double) * (grid + 1), ctx->stream);
+  k_trace_band<<<grid, 256, 0, ctx->stream>>>(M->leaves, M->leaf_ld, M->U, M->V, M->rank, M->tree->d_lo, M->L(),
+                                               M->n(), M->cap, ab_dev, ldab, b, d.as<double>() + 1);
+  check_launch("k_trace_band");
   k_sum_ordered<<<1, 32, 0, ctx->stream>>>(d.as<double>() + 1, grid, d.as<double>());
   check_launch("k_sum_ordered");
   double h = 0.0;
