@@ -292,6 +292,21 @@ int sp_inertia_noalloc(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int
 int sp_qdwh_start(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, double* alpha,
                   double* l0);
 
+/* The paper's own start parameters (Sec. 5, Eq. (param_estimation)):
+ * alpha = normest(A - mu I), the power method on (A - mu I)^T (A - mu I) from
+ * the vector of absolute column sums, stopped at relative change <= 1e-6;
+ * l0 = ||X0||_1 / (sqrt(n) condest(X0)) with X0 = (A - mu I)/alpha and
+ * condest(X0) = ||X0||_1 est(||X0^{-1}||_1), est the 1-norm estimator of
+ * Hager with Higham's refinements (at most 5 sign-vector iterations plus the
+ * alternating-sign safeguard; the one-column case of Higham-Tisseur) using a
+ * banded LU with partial pivoting.  Estimates, not bounds: alpha may fall
+ * short of ||A - mu I||_2 and l0 may exceed sigma_min(X0).  To run QDWH with
+ * them, pass them in sp_qdwh_opts.alpha / .l0.  iters (may be NULL) receives
+ * {power iterations, LU solves}.  ab: host or device.  Synchronising;
+ * SP_EBREAKDOWN if the LU meets an exactly zero pivot (A - mu I singular). */
+int sp_qdwh_params_paper(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
+                         double* alpha, double* l0, int32_t* iters);
+
 /* ---- QR-based first iteration (Sec. 4, Algorithms 1/2, Remark "construct_off") ---- */
 
 /* Givens rotations of the fast QR of [scale * A; I] for the banded A

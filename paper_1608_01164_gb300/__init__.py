@@ -35,7 +35,7 @@ EXPORTS = [
     "sp_hodlr_trsm", "sp_inertia", "sp_locate_shift", "sp_qdwh_start", "sp_givens_generate",
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
     "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector", "sp_hodlr_level_ranks",
-    "sp_trace_product_band",
+    "sp_trace_product_band", "sp_qdwh_params_paper",
 ]
 
 
@@ -134,6 +134,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_batched_projector": (I, [P, I32, P, P, P, P, P, I32, D, I32, ctypes.POINTER(sp_qdwh_opts), I32, P, P]),
         "sp_hodlr_level_ranks": (I, [P, P, I32, P, P, ctypes.POINTER(D)]),
         "sp_trace_product_band": (I, [P, P, I32, P, I64, ctypes.POINTER(D)]),
+        "sp_qdwh_params_paper": (I, [P, I64, I32, P, I64, D, ctypes.POINTER(D), ctypes.POINTER(D), P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -323,6 +324,19 @@ def sp_qdwh_start(ctx, ab, mu: float, n=None, b=None, ldab=None):
     a, l0 = ctypes.c_double(), ctypes.c_double()
     _check(ctx, _lib.sp_qdwh_start(ctx, n, b, _ptr(ab), ldab, float(mu), ctypes.byref(a), ctypes.byref(l0)))
     return a.value, l0.value
+
+
+def sp_qdwh_params_paper(ctx, ab, mu: float, n=None, b=None, ldab=None):
+    """The paper's normest/condest start: (alpha, l0, power iterations, LU solves)."""
+    import numpy as _np
+    if n is None:
+        n, bp1 = ab.shape
+        b, ldab = bp1 - 1, bp1
+    a, l0 = ctypes.c_double(), ctypes.c_double()
+    it = _np.zeros(2, dtype=_np.int32)
+    _check(ctx, _lib.sp_qdwh_params_paper(ctx, n, b, _ptr(ab), ldab, float(mu), ctypes.byref(a), ctypes.byref(l0),
+                                          it.ctypes.data))
+    return a.value, l0.value, int(it[0]), int(it[1])
 
 
 def sp_givens_generate(ctx, n: int, b: int, ab, ldab: int, scale: float, cs):

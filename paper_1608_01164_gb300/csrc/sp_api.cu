@@ -34,6 +34,8 @@ void locate_shift(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t l
                   double* lam_nu_hi, double* lam_nu1_lo);
 void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
                 double* l0);
+void qdwh_params_paper(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
+                       double* l0, int* iters);
 void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma);
 void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
                             const double* shifts_dev, int64_t* counts_dev);
@@ -875,6 +877,21 @@ int sp_qdwh_start(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t 
     // the counts are of A - mu I's eigenvalues relative to mu: count A at
     // shifts mu +- d directly
     qdwh_start(ctx, n, b, d.as<double>(), b + 1, mu, alpha, l0);
+  });
+}
+
+int sp_qdwh_params_paper(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
+                         double* alpha, double* l0, int32_t* iters) {
+  if (!ctx || !ab || !alpha || !l0 || n < 1 || b < 0 || ldab < b + 1) return SP_EINVAL;
+  return guarded(ctx, [&] {
+    DBuf d = band_on_device(ctx, n, b, ab, ldab);
+    int it[2] = {0, 0};
+    qdwh_params_paper(ctx, n, b, d.as<double>(), b + 1, mu, alpha, l0, it);
+    check_flags(ctx, "banded LU of the 1-norm estimator");
+    if (iters) {
+      iters[0] = it[0];
+      iters[1] = it[1];
+    }
   });
 }
 

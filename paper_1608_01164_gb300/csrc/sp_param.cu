@@ -448,6 +448,376 @@ void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t lda
   *l0 = std::min(dgood / a, 1.0);
 }
 
-void configure_param_kernels() { configure_dynamic_smem(reinterpret_cast<const void*>(k_inertia_warp)); }
+// ------------------------------------------- paper's parameter estimates --
+// Eq. (param_estimation): alpha = normest(A) (power method on A^T A, relative
+// tolerance 1e-6) and l0 = ||X0||_1 / (sqrt(n) condest(X0)), X0 = A / alpha
+// (here A - mu I), condest = ||X0||_1 times a 1-norm estimate of X0^{-1}
+// (Hager's method with Higham's refinements, the one-column case of the
+// Higham-Tisseur estimator) from a banded LU with partial pivoting.  These
+// are estimates: alpha can fall short of ||A - mu I||_2 and l0 can exceed
+// sigma_min(X0); the library's default start uses inertia brackets instead.
+
+// y = (A - mu I) x for the symmetric band (lower storage), one row per thread.
+__global__ void k_band_matvec(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, double mu,
+                              const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = (ab[i * ldab] - mu) * x[i];
+    for (int d = 1; d <= b; ++d) {
+      if (i - d >= 0) s = fma(ab[d + (i - d) * ldab], x[i - d], s);
+      if (i + d < n) s = fma(ab[d + i * ldab], x[i + d], s);
+    }
+    y[i] = s;
+  }
+}
+
+// Per-block partial reductions of x (kind 0: sum x^2, 1: sum |x|, 2: max |x|
+// with its index encoded after the value), summed on the host in block order.
+__global__ void __launch_bounds__(256) k_reduce_parts(const double* __restrict__ x, int64_t n, int kind,
+                                                      double* part) {
+  __shared__ double rv[8];
+  __shared__ int64_t ri[8];
+  double v = 0.0;
+  int64_t vi = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = x[i];
+    if (kind == 0) v = fma(a, a, v);
+    else if (kind == 1) v += fabs(a);
+    else if (fabs(a) > v) {
+      v = fabs(a);
+      vi = i;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int64_t oi = __shfl_xor_sync(0xffffffffu, vi, o);
+    if (kind == 2) {
+      if (ov > v || (ov == v && oi < vi)) {
+        v = ov;
+        vi = oi;
+      }
+    } else {
+      v += ov;
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+    rv[threadIdx.x >> 5] = v;
+    ri[threadIdx.x >> 5] = vi;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = rv[0];
+    int64_t ti = ri[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      if (kind == 2) {
+        if (rv[w] > t || (rv[w] == t && ri[w] < ti)) {
+          t = rv[w];
+          ti = ri[w];
+        }
+      } else {
+        t += rv[w];
+      }
+    }
+    part[2 * blockIdx.x] = t;
+    part[2 * blockIdx.x + 1] = (double)ti;
+  }
+}
+
+__global__ void k_scale_vec(double* x, int64_t n, double s) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    x[i] *= s;
+}
+
+// x_i = |a_ii - mu| + sum_{j != i} |a_ij|: the column sums of |A - mu I| (the
+// power method's start vector; their maximum is ||A - mu I||_1).
+__global__ void k_band_colsum(const double* __restrict__ ab, int64_t ldab, int64_t n, int b, double mu, double* x) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = fabs(ab[i * ldab] - mu);
+    for (int d = 1; d <= b; ++d) {
+      if (i - d >= 0) s += fabs(ab[d + (i - d) * ldab]);
+      if (i + d < n) s += fabs(ab[d + i * ldab]);
+    }
+    x[i] = s;
+  }
+}
+
+// Banded LU with partial pivoting of A - mu I (bandwidth b; U gets 2b
+// superdiagonals) by one warp.  The active window, rows j..j+b by columns
+// j..j+2b, lives in shared memory as a ring over row and column indices.
+// Outputs: U row j (2b+1 entries from the diagonal) at Uf[j (2b+1) + k], the
+// b multipliers of step j at Lf[j b + t], the pivot row piv[j] in [j, j+b].
+// A zero pivot sets flags[FLAG_BREAKDOWN] (the step then leaves the column).
+__global__ void __launch_bounds__(32) k_band_lu(const double* __restrict__ ab, int64_t ldab, int64_t n, int b,
+                                                double mu, double* Uf, double* Lf, int64_t* piv, int* flags) {
+  extern __shared__ double win[];
+  const int R = b + 1, C = 2 * b + 1;
+  const int lane = threadIdx.x;
+  auto at = [&](int64_t r, int64_t c) -> double& { return win[(int)(r % R) * C + (int)(c % C)]; };
+  auto A = [&](int64_t r, int64_t c) -> double {  // entry of A - mu I
+    if (r < 0 || c < 0 || r >= n || c >= n) return 0.0;
+    const int64_t d = r > c ? r - c : c - r;
+    if (d > b) return 0.0;
+    const int64_t lo = r > c ? c : r;
+    return ab[d + lo * ldab] - (r == c ? mu : 0.0);
+  };
+  // initial window: rows 0..b-1, columns 0..2b (row b arrives at step 0)
+  for (int e = lane; e < R * C; e += 32) win[e] = 0.0;
+  __syncwarp();
+  for (int e = lane; e < b * C; e += 32) {
+    const int r = e / C, c = e % C;
+    at(r, c) = A(r, c);
+  }
+  __syncwarp();
+  for (int64_t j = 0; j < n; ++j) {
+    // row j+b enters (columns j..j+2b); column j+2b is zero in the other rows
+    const int64_t rn = j + b;
+    for (int c = lane; c < C; c += 32) {
+      const int64_t col = j + c;
+      at(rn, col) = (rn < n) ? A(rn, col) : 0.0;
+    }
+    for (int r = lane; r < b; r += 32) at(j + r, j + 2 * b) = 0.0;
+    __syncwarp();
+    // pivot: largest |entry| of column j among rows j..min(j+b, n-1)
+    const int64_t rlast = (j + b < n) ? j + b : n - 1;
+    double best = -1.0;
+    int64_t bi = j;
+    for (int64_t r = j + lane; r <= rlast; r += 32) {
+      const double v = fabs(at(r, j));
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+      const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ov > best || (ov == best && oi < bi)) {
+        best = ov;
+        bi = oi;
+      }
+    }
+    if (bi != j)
+      for (int c = lane; c < C; c += 32) {
+        const double t = at(j, j + c);
+        at(j, j + c) = at(bi, j + c);
+        at(bi, j + c) = t;
+      }
+    __syncwarp();
+    const double u = at(j, j);
+    if (lane == 0) {
+      piv[j] = bi;
+      if (u == 0.0) atomicOr(&flags[FLAG_BREAKDOWN], 1);
+    }
+    double inv = 0.0;
+    if (lane == 0 && u != 0.0) inv = 1.0 / u;
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    // multipliers and the update of rows j+1..rlast, columns j+1..j+2b
+    const int nr = (int)(rlast - j);
+    for (int e = lane; e < nr * 2 * b; e += 32) {
+      const int t = e / (2 * b), c = e % (2 * b);
+      const int64_t r = j + 1 + t, col = j + 1 + c;
+      at(r, col) = fma(-at(r, j) * inv, at(j, col), at(r, col));
+    }
+    __syncwarp();
+    for (int t = lane; t < b; t += 32) {
+      const int64_t r = j + 1 + t;
+      Lf[j * b + t] = (t < nr) ? at(r, j) * inv : 0.0;
+    }
+    for (int c = lane; c < C; c += 32) Uf[j * C + c] = (j + c < n) ? at(j, j + c) : 0.0;
+    __syncwarp();
+  }
+}
+
+// Solves (A - mu I) x = y in place with the banded LU (one thread; the
+// substitutions are dependent chains).
+__global__ void k_band_lu_solve(const double* __restrict__ Uf, const double* __restrict__ Lf,
+                                const int64_t* __restrict__ piv, int64_t n, int b, double* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int C = 2 * b + 1;
+  for (int64_t j = 0; j < n; ++j) {
+    const int64_t p = piv[j];
+    if (p != j) {
+      const double t = y[j];
+      y[j] = y[p];
+      y[p] = t;
+    }
+    const double yj = y[j];
+    for (int t = 0; t < b && j + 1 + t < n; ++t) y[j + 1 + t] = fma(-Lf[j * b + t], yj, y[j + 1 + t]);
+  }
+  for (int64_t j = n - 1; j >= 0; --j) {
+    double s = y[j];
+    for (int k = 1; k < C && j + k < n; ++k) s = fma(-Uf[j * C + k], y[j + k], s);
+    const double u = Uf[j * C];
+    y[j] = (u != 0.0) ? s / u : 0.0;
+  }
+}
+
+__global__ void k_fill_hager(double* x, int64_t n, int mode, int64_t jdx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    if (mode == 0) x[i] = 1.0 / (double)n;                       // uniform start
+    else if (mode == 1) x[i] = (i == jdx) ? 1.0 : 0.0;           // unit vector e_j
+    else x[i] = ((i & 1) ? -1.0 : 1.0) * (1.0 + (n > 1 ? (double)i / (double)(n - 1) : 0.0));  // alternating
+  }
+}
+
+// xi = sign(y) (+1 for y >= 0); *changed = 1 if any entry differs from xi_old
+__global__ void k_sign_vec(const double* __restrict__ y, double* xi, int64_t n, int* changed) {
+  bool ch = false;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double s = y[i] >= 0.0 ? 1.0 : -1.0;
+    ch |= (s != xi[i]);
+    xi[i] = s;
+  }
+  if (__any_sync(0xffffffffu, ch) && (threadIdx.x & 31) == 0) atomicOr(changed, 1);
+}
+
+namespace {
+struct Reducer {
+  sp_ctx* ctx;
+  int grid;
+  DBuf parts;
+  explicit Reducer(sp_ctx* c, int64_t n)
+      : ctx(c), grid((int)std::min<int64_t>((n + 255) / 256, 512)), parts((size_t)2 * 512 * sizeof(double), c->stream) {}
+  // kind 0: sum of squares, 1: sum |x|, 2: (max |x|, index)
+  std::pair<double, int64_t> run(const double* x, int64_t n, int kind) {
+    k_reduce_parts<<<grid, 256, 0, ctx->stream>>>(x, n, kind, parts.as<double>());
+    check_launch("k_reduce_parts");
+    std::vector<double> h(2 * grid);
+    check_cuda(cudaMemcpyAsync(h.data(), parts.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream),
+               "parts");
+    check_cuda(cudaStreamSynchronize(ctx->stream), "sync");
+    double v = (kind == 2) ? -1.0 : 0.0;
+    int64_t vi = 0;
+    for (int g = 0; g < grid; ++g) {
+      if (kind == 2) {
+        if (h[2 * g] > v) {
+          v = h[2 * g];
+          vi = (int64_t)h[2 * g + 1];
+        }
+      } else {
+        v += h[2 * g];
+      }
+    }
+    return {v, vi};
+  }
+};
+}  // namespace
+
+void qdwh_params_paper(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
+                       double* l0, int* iters) {
+  cudaStream_t st = ctx->stream;
+  const int g = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  DBuf x(sizeof(double) * n, st), y(sizeof(double) * n, st), xi(sizeof(double) * n, st);
+  Reducer red(ctx, n);
+  // ---- normest: x = column sums of |A|, normalised; e = ||A x||/||x|| until
+  // the relative change is <= 1e-6 (x <- A^T A x, normalised)
+  k_band_colsum<<<g, 256, 0, st>>>(ab_dev, ldab, n, b, mu, x.as<double>());
+  check_launch("k_band_colsum");
+  const double norm1 = red.run(x.as<double>(), n, 2).first;  // ||A - mu I||_1 (symmetric: max column sum)
+  double e = std::sqrt(red.run(x.as<double>(), n, 0).first);
+  int pit = 0;
+  if (e > 0.0) {
+    k_scale_vec<<<g, 256, 0, st>>>(x.as<double>(), n, 1.0 / e);
+    check_launch("k_scale_vec");
+    double e0 = 0.0;
+    while (std::fabs(e - e0) > 1e-6 * e && pit < 100) {
+      e0 = e;
+      k_band_matvec<<<g, 256, 0, st>>>(ab_dev, ldab, n, b, mu, x.as<double>(), y.as<double>());
+      check_launch("k_band_matvec");
+      const double ny = std::sqrt(red.run(y.as<double>(), n, 0).first);
+      const double nx = std::sqrt(red.run(x.as<double>(), n, 0).first);
+      e = ny / nx;
+      k_band_matvec<<<g, 256, 0, st>>>(ab_dev, ldab, n, b, mu, y.as<double>(), x.as<double>());
+      check_launch("k_band_matvec");
+      const double nn = std::sqrt(red.run(x.as<double>(), n, 0).first);
+      if (nn == 0.0) break;
+      k_scale_vec<<<g, 256, 0, st>>>(x.as<double>(), n, 1.0 / nn);
+      check_launch("k_scale_vec");
+      ++pit;
+    }
+  }
+  const double a = e;
+  if (!(a > 0.0)) fail(SP_EINVAL, "normest: A - mu I is zero");
+  // ---- 1-norm estimate of (A - mu I)^{-1} from the banded LU
+  const int C = 2 * b + 1;
+  DBuf Uf(sizeof(double) * (size_t)n * C, st), Lf(sizeof(double) * (size_t)n * std::max(b, 1), st);
+  DBuf pv(sizeof(int64_t) * (size_t)n, st);
+  const size_t sm = sizeof(double) * (size_t)(b + 1) * C;
+  ensure_dynamic_smem(reinterpret_cast<const void*>(k_band_lu), sm);
+  k_band_lu<<<1, 32, sm, st>>>(ab_dev, ldab, n, b, mu, Uf.as<double>(), Lf.as<double>(), pv.as<int64_t>(),
+                               ctx->d_flags);
+  check_launch("k_band_lu");
+  int nsolve = 0;
+  auto solve = [&](double* v) {
+    k_band_lu_solve<<<1, 32, 0, st>>>(Uf.as<double>(), Lf.as<double>(), pv.as<int64_t>(), n, b, v);
+    check_launch("k_band_lu_solve");
+    ++nsolve;
+  };
+  DBuf chg(sizeof(int), st);
+  double est;
+  if (n == 1) {
+    k_fill_hager<<<1, 32, 0, st>>>(y.as<double>(), n, 0, 0);
+    solve(y.as<double>());
+    est = red.run(y.as<double>(), n, 1).first;
+  } else {
+    k_fill_hager<<<g, 256, 0, st>>>(y.as<double>(), n, 0, 0);
+    check_launch("k_fill_hager");
+    solve(y.as<double>());
+    est = red.run(y.as<double>(), n, 1).first;
+    check_cuda(cudaMemsetAsync(xi.p, 0, sizeof(double) * n, st), "memset");
+    check_cuda(cudaMemsetAsync(chg.p, 0, sizeof(int), st), "memset");
+    k_sign_vec<<<g, 256, 0, st>>>(y.as<double>(), xi.as<double>(), n, chg.as<int>());
+    check_launch("k_sign_vec");
+    check_cuda(cudaMemcpyAsync(x.p, xi.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+    solve(x.as<double>());  // z = A^{-T} xi = A^{-1} xi (symmetric)
+    int64_t jdx = red.run(x.as<double>(), n, 2).second;
+    for (int it = 2; it <= 5; ++it) {
+      k_fill_hager<<<g, 256, 0, st>>>(y.as<double>(), n, 1, jdx);
+      check_launch("k_fill_hager");
+      solve(y.as<double>());
+      const double est_old = est;
+      est = red.run(y.as<double>(), n, 1).first;
+      check_cuda(cudaMemsetAsync(chg.p, 0, sizeof(int), st), "memset");
+      k_sign_vec<<<g, 256, 0, st>>>(y.as<double>(), xi.as<double>(), n, chg.as<int>());
+      check_launch("k_sign_vec");
+      int changed = 0;
+      check_cuda(cudaMemcpyAsync(&changed, chg.p, sizeof(int), cudaMemcpyDeviceToHost, st), "flag");
+      check_cuda(cudaStreamSynchronize(st), "sync");
+      if (!changed || est <= est_old) {
+        est = std::max(est, est_old);
+        break;
+      }
+      check_cuda(cudaMemcpyAsync(x.p, xi.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "copy");
+      solve(x.as<double>());
+      const auto zm = red.run(x.as<double>(), n, 2);
+      // stop when the largest |z| sits at the previous index
+      std::vector<double> zj(1);
+      check_cuda(cudaMemcpyAsync(zj.data(), x.as<double>() + jdx, sizeof(double), cudaMemcpyDeviceToHost, st), "z");
+      check_cuda(cudaStreamSynchronize(st), "sync");
+      if (std::fabs(zj[0]) == zm.first) break;
+      jdx = zm.second;
+    }
+    // alternating-sign vector (Higham's safeguard)
+    k_fill_hager<<<g, 256, 0, st>>>(y.as<double>(), n, 2, 0);
+    check_launch("k_fill_hager");
+    solve(y.as<double>());
+    const double alt = 2.0 * red.run(y.as<double>(), n, 1).first / (3.0 * (double)n);
+    est = std::max(est, alt);
+  }
+  // X0 = (A - mu I)/alpha: ||X0||_1 = norm1/alpha, ||X0^{-1}||_1 ~ alpha est,
+  // condest(X0) = ||X0||_1 ||X0^{-1}||_1, l0 = ||X0||_1 / (sqrt(n) condest)
+  const double x0n1 = norm1 / a;
+  const double cond = x0n1 * (a * est);
+  *alpha = a;
+  *l0 = x0n1 / (std::sqrt((double)n) * cond);
+  if (iters) {
+    iters[0] = pit;
+    iters[1] = nsolve;
+  }
+}
+
+void configure_param_kernels() {
+  configure_dynamic_smem(reinterpret_cast<const void*>(k_inertia_warp));
+  configure_dynamic_smem(reinterpret_cast<const void*>(k_band_lu));
+}
 
 }  // namespace sp

@@ -1,0 +1,100 @@
+"""Accuracy versus spectral gap and versus truncation tolerance on the paper's
+own synthetic matrices (Sec. 6.1: banded matrices with eigenvalues equispaced
+in [-1, -gap] and [gap, 1], so mu = 0, nu = n/2), as in the paper's accuracy
+examples for tridiagonal (Sec. 6.2) and banded matrices (Sec. 6.3).
+
+For each case the GPU projector P (through the C ABI) gives U = I - 2P and the
+error measures of Eq. (error_measures): e_id = ||U^2 - I||_2,
+e_trace = |tr U - tr sign(A)|, e_SP = ||P - Pi||_2 with Pi from the oracle's
+dense eigensolver.  The dense QDWH oracle with one QR-based step gives the
+reference error level of the iteration itself (Table 1 of the paper: it grows
+like u/gap); hQDWH must stay within a modest factor of max(that, tol).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import sp_inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1608_01164_gb300 as sp  # noqa: E402
+
+N = 512
+LEAF = 64
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    sp.load()
+    c = sp.sp_ctx_create(0)
+    yield c
+    sp.sp_ctx_destroy(c)
+
+
+_cache = {}
+
+
+def case(gap, b):
+    """Band, exact projector, dense-QDWH oracle errors for one (gap, b)."""
+    key = (gap, b)
+    if key not in _cache:
+        lam = sp_inputs.gap_spectrum(N, gap)
+        ab = sp_inputs.prescribed_band(lam, b)
+        A = oracle.band_to_dense(ab)
+        Pi, nu, _ = oracle.projector(ab, 0.0)
+        alpha = 1.0 * (1 + 1e-10)
+        l0 = gap / alpha * (1 - 1e-6)
+        q = oracle.qdwh_dense(A, alpha, l0)
+        dense_err = oracle.error_measures(q.U, A, Pi, nu)
+        _cache[key] = (ab, A, Pi, nu, dense_err)
+    return _cache[key]
+
+
+def hqdwh_errors(ctx, ab, A, Pi, nu, tol):
+    n = ab.shape[0]
+    H = sp.sp_hodlr_from_band(ctx, ab, 0.0, LEAF, tol)
+    S, info = sp.sp_qdwh_sign(ctx, H)
+    P = sp.sp_projector(ctx, S)
+    try:
+        Pd = np.zeros((n, n), order="F")
+        sp.sp_to_dense(ctx, P, 0, n, Pd, n)
+        U = np.eye(n) - 2.0 * Pd
+        return oracle.error_measures(U, A, Pi, nu), info
+    finally:
+        for h in (H, S, P):
+            sp.sp_hodlr_destroy(h)
+
+
+@pytest.mark.parametrize("b", [1, 4])
+@pytest.mark.parametrize("gap", [1e-1, 1e-4, 1e-8])
+def test_accuracy_versus_gap(ctx, gap, b):
+    ab, A, Pi, nu, (d_id, d_tr, d_sp) = case(gap, b)
+    (e_id, e_tr, e_sp), info = hqdwh_errors(ctx, ab, A, Pi, nu, 1e-10)
+    print(f"gap {gap:.0e} b={b}: hQDWH e_id {e_id:.2e} e_trace {e_tr:.2e} e_SP {e_sp:.2e} "
+          f"(dense QDWH e_SP {d_sp:.2e}) iters {info.iters} max rank {info.max_rank}")
+    assert e_tr <= 1e-8
+    assert e_id <= 1e-8
+    assert e_sp <= max(1e-8, 100.0 * d_sp), (e_sp, d_sp)
+
+
+def test_accuracy_versus_tolerance(ctx):
+    """e_SP falls with the truncation tolerance until the iteration's own
+    rounding level (gap 1e-4, tridiagonal)."""
+    ab, A, Pi, nu, (_, _, d_sp) = case(1e-4, 1)
+    errs = []
+    ranks = []
+    for tol in (1e-6, 1e-8, 1e-10, 1e-12, 1e-14):
+        (e_id, e_tr, e_sp), info = hqdwh_errors(ctx, ab, A, Pi, nu, tol)
+        errs.append(e_sp)
+        ranks.append(info.max_rank)
+        print(f"tol {tol:.0e}: e_id {e_id:.2e} e_trace {e_tr:.2e} e_SP {e_sp:.2e} max rank {info.max_rank}")
+    floor = max(d_sp, 1e-13)
+    for k in range(1, len(errs)):
+        assert errs[k] <= 2.0 * max(errs[k - 1], floor), errs
+    assert errs[-1] <= max(1e-10, 100.0 * d_sp), errs
+    assert errs[0] > errs[-1]
+    assert ranks == sorted(ranks)
