@@ -222,21 +222,23 @@ __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int r
     }
 }
 
+// te: edge of the output tiles the grid is laid out in (64, or 16 for small
+// problems, so that their few outputs still spread over many SMs).
 template <bool TA, bool TB, typename MT>
-__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int split,
+__global__ void __launch_bounds__(256) k_gemm(const GemmTask* __restrict__ tasks, int kchunk, int split, int te,
                                               double* fc) {
   const GemmTask t = tasks[blockIdx.y];
   const int m = dsize(t.m, t.pm), n = dsize(t.n, t.pn), k = dsize(t.k, t.pk);
-  const int tiles_m = (m + kGT - 1) / kGT;
+  const int tiles_m = (m + te - 1) / te;
   const int tile = blockIdx.x;
-  if (tile >= tiles_m * ((n + kGT - 1) / kGT)) return;
-  const int row0 = (tile % tiles_m) * kGT, col0 = (tile / tiles_m) * kGT;
+  if (tile >= tiles_m * ((n + te - 1) / te)) return;
+  const int row0 = (tile % tiles_m) * te, col0 = (tile / tiles_m) * te;
   const int kbeg = blockIdx.z * kchunk;
   const int kend = min(k, kbeg + kchunk);
   if (kbeg >= kend && blockIdx.z > 0) return;
   __shared__ MT As[kGK][kGT + 1];
   __shared__ MT Bs[kGK][kGT + 1];
-  const int em = min(kGT, m - row0), en = min(kGT, n - col0);
+  const int em = min(te, m - row0), en = min(te, n - col0);
   const int mi = em <= 16 ? 1 : (em <= 32 ? 2 : 4);
   const int mj = en <= 16 ? 1 : (en <= 32 ? 2 : 4);
   switch (mi * 8 + mj) {
@@ -709,13 +711,22 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
   }
   if (tasks.empty()) return;
   int nz = 1, kchunk = std::max(maxk, 1);
+  // binary64 runs at about 8 GFLOP/s per SM on this part, so a GEMM spread
+  // over a few CTAs is compute-bound on a few SMs.  Small problems (fewer
+  // 64 x 64 tiles than SMs) are laid out in 16 x 16 tiles instead, and k is
+  // split (chunks of at least 32, resp. 64) until the grid covers the GPU.
+  int te = kGT;
+  int64_t ctas = (int64_t)maxtiles * (int64_t)tasks.size();
+  if (ksplit <= 0 && ctas < ctx->num_sms) {
+    te = 16;
+    maxtiles = 0;
+    for (const auto& t : tasks) maxtiles = std::max(maxtiles, ((t.m + 15) / 16) * ((t.n + 15) / 16));
+    ctas = (int64_t)maxtiles * (int64_t)tasks.size();
+  }
+  const int kmin = te == kGT ? 64 : 32;
   if (ksplit <= 0) {
-    const int64_t ctas = (int64_t)maxtiles * (int64_t)tasks.size();
-    // binary64 runs at about 8 GFLOP/s per SM on this part, so a GEMM spread
-    // over a few CTAs is compute-bound on a few SMs: split k (chunks of at
-    // least 64) until the grid covers the GPU
-    if (maxk >= 128 && ctas < 2 * ctx->num_sms) {
-      nz = (int)std::min<int64_t>((4 * ctx->num_sms + ctas - 1) / ctas, maxk / 64);
+    if (maxk >= 2 * kmin && ctas < 2 * ctx->num_sms) {
+      nz = (int)std::min<int64_t>((4 * ctx->num_sms + ctas - 1) / ctas, maxk / kmin);
       nz = std::max(nz, 1);
     }
   } else {
@@ -750,15 +761,15 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
     const int sp = nz > 1 ? 1 : 0;
     if (ctx->gemm_fp32) {
-      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
     } else {
-      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
-      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, fc);
+      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
     }
     check_launch("k_gemm");
     if (nz > 1) {
