@@ -401,38 +401,60 @@ __global__ void __launch_bounds__(1024) k_leaf_potrf(const LeafTask* __restrict_
   }
 }
 
-// ------------------------------------------- leaf Cholesky on a cluster ----
-// Blocked right-looking Cholesky (16 x 16 blocks) of one leaf by a cluster of
-// kCC CTAs on kCC SMs.  Binary64 runs at about two FMAs per clock per SM on
-// this part, so a single SM needs ~0.3 ms for a 195-row leaf, and the leaf
-// factorisations form the H-Cholesky's sequential critical path.  Block step p:
-//  (a) CTA p % kCC factors the diagonal block with one warp (row i of the
-//      block in lane i's registers, one reciprocal square root per column)
-//      and forms the block's inverse in its shared memory;
-//  (b) cluster barrier; the row blocks below are dealt over the cluster and
-//      each becomes L_ip = A_ip L_pp^{-T}, reading L_pp^{-1} from the owner's
-//      shared memory (distributed shared memory);
-//  (c) cluster barrier; the trailing blocks A_ij -= L_ip L_jp^T (p < j <= i)
-//      are dealt round-robin over the cluster;
-//  (d) cluster barrier.
-// The leaf stays in global memory (resident in L2); the cluster barriers
-// (release/acquire at cluster scope) order the CTAs' writes.  The strict
-// upper triangle is zeroed at the end.  A non-positive pivot sets the
-// breakdown flag and continues with pivot 1, as k_leaf_potrf does.
-constexpr int kCB = 16;              // block edge
-constexpr int kCC = 8;               // CTAs per cluster (portable cluster size)
-constexpr int kCMaxN = kCB * 16;     // largest leaf handled (16 block rows)
+// ----------------------------- leaf Cholesky and inverse on a cluster ----
+// L = chol(A) and X = L^{-1} of one leaf (n <= 256) by a cluster of kCC CTAs
+// on kCC SMs, blocked in 16 x 16 blocks.  Binary64 runs at about two FMAs per
+// clock per SM on this part, so one SM needs ~0.3 ms for the factorisation of
+// a 195-row leaf alone, and the leaf factorisations form the H-Cholesky's
+// sequential critical path.
+//
+// The lower-triangular blocks of A (and of the inverse's work array B, which
+// starts as I) are dealt over the cluster by their row-major index q: block q
+// lives in CTA q % kCC, slot q / kCC of its shared memory, and its owner does
+// every update of it.  Other CTAs read it through distributed shared memory.
+// Right-looking block step p (two cluster barriers per step):
+//  (B) L_ip = A_ip L_pp^{-T} for the blocks below the diagonal block, and the
+//      inverse's row block X_pj = L_pp^{-1} B_pj (forward substitution of
+//      L X = I, Sec. "H-Cholesky" inverse factor); barrier;
+//  (C) each CTA copies the column panel L_.p and the row panel X_p. into its
+//      own shared memory and applies its blocks' updates
+//      A_ij -= L_ip L_jp^T (p < j <= i) and B_ij -= L_ip X_pj (i > p, j <= p);
+//      the owner of block (p+1, p+1) updates it first and factors it at once
+//      (one warp, row i of the block in lane i's registers, a reciprocal
+//      square root per column), so the next diagonal factorisation overlaps
+//      the other CTAs' updates; barrier.
+// Rows beyond n are padded as identity.  A non-positive pivot sets the
+// breakdown flag and continues with pivot 1.
+constexpr int kCB = 16;                                                  // block edge
+constexpr int kCC = 8;                                                   // CTAs per cluster (portable)
+constexpr int kCMaxNB = 16;                                              // block rows: n <= 256
+constexpr int kCMaxN = kCB * kCMaxNB;
+constexpr int kCSlots = (kCMaxNB * (kCMaxNB + 1) / 2 + kCC - 1) / kCC;  // blocks per CTA
+constexpr int kCP = kCB + 1;                                             // padded row
 
-// Factor the pb x pb diagonal block at D (lower triangle; pb <= kCB) in place
-// and write its inverse to Linv (row-major, zero above the diagonal).  Called
-// by one full warp; lanes 16..31 mirror lanes 0..15 and write nothing.
-__device__ __noinline__ void cluster_diag_block(double* D, int64_t lda, int pb, double (*Linv)[kCB + 1], int* flags) {
+struct ClusterSmem {
+  double A[kCSlots][kCB][kCP];    // owned blocks of A, then L
+  double X[kCSlots][kCB][kCP];    // owned blocks of B, then X = L^{-1}
+  double Lpan[kCMaxNB][kCB][kCP];  // column panel L_ip of the current step
+  double Xpan[kCMaxNB][kCB][kCP];  // row panel X_pj of the current step
+  double Linv[kCB][kCP];           // inverse of this CTA's latest diagonal block
+  double Lcp[kCB][kCP];            // copy of the current step's L_pp^{-1}
+};
+
+__device__ __forceinline__ int blk_q(int i, int j) { return i * (i + 1) / 2 + j; }
+__device__ __forceinline__ int blk_owner(int i, int j) { return blk_q(i, j) % kCC; }
+__device__ __forceinline__ int blk_slot(int i, int j) { return blk_q(i, j) / kCC; }
+
+// Factor the 16 x 16 diagonal block D (row-major, ld kCP, lower triangle) in
+// place and write its inverse to Linv (zero above the diagonal).  One full
+// warp; lanes 16..31 mirror lanes 0..15 and write nothing.
+__device__ __noinline__ void cluster_diag_block(double* D, double (*Linv)[kCP], int* flags) {
   const unsigned full = 0xffffffffu;
   const int i = threadIdx.x & 15;
   const bool writer = (threadIdx.x & 31) < 16;
   double row[kCB];
 #pragma unroll
-  for (int k = 0; k < kCB; ++k) row[k] = (i < pb && k <= i) ? D[i + (int64_t)k * lda] : (k == i ? 1.0 : 0.0);
+  for (int k = 0; k < kCB; ++k) row[k] = (k <= i) ? D[i * kCP + k] : 0.0;
   double yi = 1.0;  // 1 / L_ii of this lane's row
   bool bad = false;
 #pragma unroll
@@ -456,8 +478,8 @@ __device__ __noinline__ void cluster_diag_block(double* D, int64_t lda, int pb, 
     }
   }
   if (bad && threadIdx.x == 0) atomicOr(&flags[FLAG_BREAKDOWN], 1);
-  // inverse by columns of the substitution: s_i[j] = sum_{k<i} L_ik X_kj,
-  // row k of X final once every k' < k has been added (X_kk = 1/L_kk)
+  // inverse by columns of the substitution: x_i[j] = sum_{k<i} L_ik X_kj;
+  // row k of X is final once every k' < k has been added (X_kk = 1/L_kk)
   double x[kCB];
 #pragma unroll
   for (int j = 0; j < kCB; ++j) x[j] = 0.0;
@@ -478,70 +500,156 @@ __device__ __noinline__ void cluster_diag_block(double* D, int64_t lda, int pb, 
 #pragma unroll
     for (int k = 0; k < kCB; ++k) {
       Linv[i][k] = (k <= i) ? x[k] : 0.0;
-      if (i < pb && k <= i) D[i + (int64_t)k * lda] = row[k];
+      D[i * kCP + k] = (k <= i) ? row[k] : 0.0;
     }
   }
 }
 
+// The diagonal step of the block's owner: factor, then X_pp = L_pp^{-1}.
+__device__ void cluster_diag_step(ClusterSmem& S, int p, int* flags) {
+  const int sl = blk_slot(p, p);
+  if (threadIdx.x < 32) cluster_diag_block(&S.A[sl][0][0], S.Linv, flags);
+  __syncthreads();
+  const int r = threadIdx.x & 15, c = threadIdx.x >> 4;
+  S.X[sl][r][c] = S.Linv[r][c];
+  __syncthreads();
+}
+
 __global__ void __cluster_dims__(kCC, 1, 1) __launch_bounds__(256)
-    k_leaf_potrf_cluster(const LeafTask* __restrict__ tasks, int* flags, double* fc) {
+    k_leaf_chol_inv_cluster(const LeafTask* __restrict__ tasks, int* flags, double* fc_potrf, double* fc_inv) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ClusterSmem& S = *reinterpret_cast<ClusterSmem*>(smem_raw);
   const int rank = (int)cl.block_rank();
   const LeafTask t = tasks[blockIdx.y];
-  double* A = t.A;
-  const int64_t lda = t.lda;
   const int n = t.n;
   const int NB = (n + kCB - 1) / kCB;
-  __shared__ double Linv[kCB][kCB + 1];
-  __shared__ double Bi[kCB][kCB + 1];
-  __shared__ double Bj[kCB][kCB + 1];
+  const int nq = NB * (NB + 1) / 2;
   const int tid = threadIdx.x;
   const int r = tid & 15, c = tid >> 4;  // 256 threads = one 16 x 16 block
-  if (fc && rank == 0 && tid == 0) atomicAdd(fc, (double)n * n * n / 3.0 + (double)n * n / 2.0 + n / 6.0);
+  if (rank == 0 && tid == 0) {
+    const double dn = (double)n;
+    if (fc_potrf) atomicAdd(fc_potrf, dn * dn * dn / 3.0 + dn * dn / 2.0 + dn / 6.0);
+    // triangular inverse: sum over columns of m^2, m = n - c  ->  n(n+1)(2n+1)/6
+    if (fc_inv) atomicAdd(fc_inv, dn * (dn + 1.0) * (2.0 * dn + 1.0) / 6.0);
+  }
+  // owned blocks: A (lower triangle; rows beyond n padded as identity), B = I
+  for (int q = rank; q < nq; q += kCC) {
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    const int j = q - i * (i + 1) / 2;
+    const int gr = i * kCB + r, gc = j * kCB + c;
+    double a;
+    if (gr < n && gc < n) a = (i != j || r >= c) ? t.A[gr + (int64_t)gc * t.lda] : 0.0;
+    else a = (gr == gc) ? 1.0 : 0.0;
+    S.A[q / kCC][r][c] = a;
+    S.X[q / kCC][r][c] = (i == j && r == c) ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  if (rank == blk_owner(0, 0)) cluster_diag_step(S, 0, flags);
+  cl.sync();
   for (int p = 0; p < NB; ++p) {
-    const int p0 = p * kCB;
-    const int pb = min(kCB, n - p0);
-    const int owner = p % kCC;
-    if (rank == owner && tid < 32) cluster_diag_block(A + p0 + (int64_t)p0 * lda, lda, pb, Linv, flags);
-    cl.sync();
-    // (b) L_ip = A_ip L_pp^{-T}
-    const double* Lo = cl.map_shared_rank(&Linv[0][0], owner);
-    for (int i = p + 1 + rank; i < NB; i += kCC) {
-      const int i0 = i * kCB, ib = min(kCB, n - i0);
-      Bi[r][c] = (r < ib && c < pb) ? A[(i0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
-      __syncthreads();
-      double acc = 0.0;
+    // (B) L_ip = A_ip L_pp^{-T} (i > p); X_pj = L_pp^{-1} B_pj (j < p)
+    const double* Lo = cl.map_shared_rank(&S.Linv[0][0], blk_owner(p, p));
+    S.Lcp[r][c] = Lo[r * kCP + c];
+    __syncthreads();
+    for (int i = p + 1; i < NB; ++i) {
+      if (blk_owner(i, p) != rank) continue;
+      double(*Bk)[kCP] = S.A[blk_slot(i, p)];
+      double a0 = 0.0, a1 = 0.0;
 #pragma unroll
-      for (int k = 0; k < kCB; ++k) acc = fma(Bi[r][k], Lo[c * (kCB + 1) + k], acc);
-      if (r < ib && c < pb) A[(i0 + r) + (int64_t)(p0 + c) * lda] = acc;
+      for (int k = 0; k < kCB; k += 2) {
+        a0 = fma(Bk[r][k], S.Lcp[c][k], a0);
+        a1 = fma(Bk[r][k + 1], S.Lcp[c][k + 1], a1);
+      }
+      __syncthreads();
+      Bk[r][c] = a0 + a1;
+      __syncthreads();
+    }
+    for (int j = 0; j < p; ++j) {
+      if (blk_owner(p, j) != rank) continue;
+      double(*Bk)[kCP] = S.X[blk_slot(p, j)];
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCB; k += 2) {
+        a0 = fma(S.Lcp[r][k], Bk[k][c], a0);
+        a1 = fma(S.Lcp[r][k + 1], Bk[k + 1][c], a1);
+      }
+      __syncthreads();
+      Bk[r][c] = a0 + a1;
       __syncthreads();
     }
     cl.sync();
-    // (c) trailing update of the blocks (i, j), p < j <= i < NB
-    const int m = NB - 1 - p;
-    const int nblk = m * (m + 1) / 2;
-    for (int q = rank; q < nblk; q += kCC) {
-      int ii = 0;
-      while ((ii + 1) * (ii + 2) / 2 <= q) ++ii;
-      const int jj = q - ii * (ii + 1) / 2;
-      const int i = p + 1 + ii, j = p + 1 + jj;
-      const int i0 = i * kCB, ib = min(kCB, n - i0);
-      const int j0 = j * kCB, jb = min(kCB, n - j0);
-      Bi[r][c] = (r < ib && c < pb) ? A[(i0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
-      Bj[r][c] = (r < jb && c < pb) ? A[(j0 + r) + (int64_t)(p0 + c) * lda] : 0.0;
-      __syncthreads();
-      double acc = 0.0;
-#pragma unroll
-      for (int k = 0; k < kCB; ++k) acc = fma(Bi[r][k], Bj[c][k], acc);
-      if (r < ib && c < jb && (i != j || r >= c)) A[(i0 + r) + (int64_t)(j0 + c) * lda] -= acc;
-      __syncthreads();
+    // (C) panels L_ip (i > p) and X_pj (j <= p) into local shared memory
+    for (int i = p + 1; i < NB; ++i) {
+      const double* src = cl.map_shared_rank(&S.A[blk_slot(i, p)][0][0], blk_owner(i, p));
+      S.Lpan[i][r][c] = src[r * kCP + c];
     }
+    for (int j = 0; j <= p; ++j) {
+      const double* src = cl.map_shared_rank(&S.X[blk_slot(p, j)][0][0], blk_owner(p, j));
+      S.Xpan[j][r][c] = src[r * kCP + c];
+    }
+    __syncthreads();
+    const int nx = p + 1;
+    if (nx < NB && blk_owner(nx, nx) == rank) {
+      double(*Ak)[kCP] = S.A[blk_slot(nx, nx)];
+      double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+      for (int k = 0; k < kCB; k += 2) {
+        a0 = fma(S.Lpan[nx][r][k], S.Lpan[nx][c][k], a0);
+        a1 = fma(S.Lpan[nx][r][k + 1], S.Lpan[nx][c][k + 1], a1);
+      }
+      if (r >= c) Ak[r][c] -= a0 + a1;
+      __syncthreads();
+      cluster_diag_step(S, nx, flags);
+    }
+    for (int i = p + 1; i < NB; ++i)
+      for (int j = p + 1; j <= i; ++j) {
+        if (blk_owner(i, j) != rank || (i == nx && j == nx)) continue;
+        double(*Ak)[kCP] = S.A[blk_slot(i, j)];
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < kCB; k += 2) {
+          a0 = fma(S.Lpan[i][r][k], S.Lpan[j][c][k], a0);
+          a1 = fma(S.Lpan[i][r][k + 1], S.Lpan[j][c][k + 1], a1);
+        }
+        if (i != j || r >= c) Ak[r][c] -= a0 + a1;
+      }
+    for (int i = p + 1; i < NB; ++i)
+      for (int j = 0; j <= p; ++j) {
+        if (blk_owner(i, j) != rank) continue;
+        double(*Xk)[kCP] = S.X[blk_slot(i, j)];
+        double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+        for (int k = 0; k < kCB; k += 2) {
+          a0 = fma(S.Lpan[i][r][k], S.Xpan[j][k][c], a0);
+          a1 = fma(S.Lpan[i][r][k + 1], S.Xpan[j][k + 1][c], a1);
+        }
+        Xk[r][c] -= a0 + a1;
+      }
     cl.sync();
   }
-  for (int64_t e = (int64_t)rank * blockDim.x + tid; e < (int64_t)n * n; e += (int64_t)kCC * blockDim.x) {
-    const int i = (int)(e % n), j = (int)(e / n);
-    if (i < j) A[i + (int64_t)j * lda] = 0.0;
+  // results: owned blocks of L and X (entries inside the leaf), then the
+  // strict upper blocks are zeroed
+  for (int q = rank; q < nq; q += kCC) {
+    int i = 0;
+    while ((i + 1) * (i + 2) / 2 <= q) ++i;
+    const int j = q - i * (i + 1) / 2;
+    const int gr = i * kCB + r, gc = j * kCB + c;
+    if (gr < n && gc < n) {
+      t.A[gr + (int64_t)gc * t.lda] = S.A[q / kCC][r][c];
+      t.X[gr + (int64_t)gc * t.ldx] = (i != j || r >= c) ? S.X[q / kCC][r][c] : 0.0;
+    }
+  }
+  for (int q = rank; q < NB * NB; q += kCC) {
+    const int i = q % NB, j = q / NB;
+    if (j <= i) continue;
+    const int gr = i * kCB + r, gc = j * kCB + c;
+    if (gr < n && gc < n) {
+      t.A[gr + (int64_t)gc * t.lda] = 0.0;
+      t.X[gr + (int64_t)gc * t.ldx] = 0.0;
+    }
   }
 }
 
@@ -821,19 +929,29 @@ void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
   DBuf d = upload(tasks, ctx->stream);
   int nmax = 1;
   for (const auto& t : tasks) nmax = std::max(nmax, t.n);
-  if (nmax <= kCMaxN) {
-    ProfScope ps(ctx, KID_POTRF);
-    k_leaf_potrf_cluster<<<dim3(kCC, (unsigned)tasks.size()), 256, 0, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags,
-                                                                                     fc_ptr(ctx, KID_POTRF));
-    check_launch("k_leaf_potrf_cluster");
-    return;
-  }
   const size_t sm = (size_t)nmax * (kPW + 1) * sizeof(double);
   ensure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf), sm);
   ProfScope ps(ctx, KID_POTRF);
   k_leaf_potrf<<<(unsigned)tasks.size(), 1024, sm, ctx->stream>>>(d.as<LeafTask>(), ctx->d_flags,
                                                                    fc_ptr(ctx, KID_POTRF));
   check_launch("k_leaf_potrf");
+}
+
+bool leaf_chol_inv(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
+  if (tasks.empty()) return true;
+  for (const auto& t : tasks)
+    if (t.n > kCMaxN || !t.X) return false;
+  for (const auto& t : tasks) ctx->flops += 2.0 * (double)t.n * t.n * t.n / 3.0;
+  for (size_t off = 0; off < tasks.size(); off += 65535) {
+    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
+    std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
+    DBuf d = upload(part, ctx->stream);
+    ProfScope ps(ctx, KID_POTRF);
+    k_leaf_chol_inv_cluster<<<dim3(kCC, (unsigned)cnt), 256, sizeof(ClusterSmem), ctx->stream>>>(
+        d.as<LeafTask>(), ctx->d_flags, fc_ptr(ctx, KID_POTRF), fc_ptr(ctx, KID_LEAF_INV));
+    check_launch("k_leaf_chol_inv_cluster");
+  }
+  return true;
 }
 
 void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
@@ -863,6 +981,7 @@ void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
 }
 
 void configure_blas_kernels() {
+  configure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_chol_inv_cluster));
   configure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_potrf));
   configure_dynamic_smem(reinterpret_cast<const void*>(k_leaf_inv_smem));
 }

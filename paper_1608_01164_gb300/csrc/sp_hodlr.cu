@@ -899,8 +899,11 @@ static void chol_rec(sp_ctx* ctx, sp_hodlr* Lf, sp_hodlr* Li, int c, double* tmp
   const long pe = node_open(ctx, Tree::level_of(c));
   if (Tree::level_of(c) == T.L) {
     const int jl = c - (1 << T.L);
-    leaf_potrf(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], nullptr, 0, 0, nullptr}});
-    leaf_inverse(ctx, Lf, Li, {c});
+    if (!leaf_chol_inv(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], Li->leaf(jl), Li->leaf_ld, (int)T.sz[c],
+                                      nullptr}})) {
+      leaf_potrf(ctx, {LeafTask{Lf->leaf(jl), Lf->leaf_ld, (int)T.sz[c], nullptr, 0, 0, nullptr}});
+      leaf_inverse(ctx, Lf, Li, {c});
+    }
     node_mark(ctx, pe, 1);
     return;
   }

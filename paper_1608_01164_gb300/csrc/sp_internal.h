@@ -265,6 +265,10 @@ struct LeafTask {
 // In-place lower Cholesky of each leaf (upper triangle zeroed); sets the
 // breakdown flag on a non-positive pivot.
 void leaf_potrf(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
+// Cholesky factor (in place, upper triangle zeroed) and its inverse (into X)
+// of each leaf in one cluster kernel; returns false, doing nothing, when a
+// leaf is too large for it (n > 256) or X is missing.
+bool leaf_chol_inv(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 // X <- L^{-1} (the whole n x n inverse) for lower-triangular leaves, n <= 1024.
 void leaf_inverse_batched(sp_ctx* ctx, const std::vector<LeafTask>& tasks);
 // Sets the context's non-finite flag if any of the `count` doubles at p is
