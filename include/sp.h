@@ -245,6 +245,10 @@ int sp_hodlr_level_ranks(sp_ctx_t ctx, sp_hodlr_t M, int32_t nlevels, int32_t* m
 
 /* C = alpha A + beta B + gamma I, recompressed at C's tolerance (A's). */
 int sp_hodlr_add(sp_ctx_t ctx, double alpha, sp_hodlr_t A, double beta, sp_hodlr_t B, double gamma, sp_hodlr_t* C);
+/* T = M^T (exact: leaves transposed, the U and V factors of sibling blocks
+ * exchanged; Sec. 3.1.1).  Used for Q2^T in the QR-based step (Eq.
+ * (qdwh_qr)). */
+int sp_hodlr_transpose(sp_ctx_t ctx, sp_hodlr_t M, sp_hodlr_t* T);
 /* C = A * B (formatted product, O(k^2 n log^2 n)). */
 int sp_hodlr_mult(sp_ctx_t ctx, sp_hodlr_t A, sp_hodlr_t B, sp_hodlr_t* C);
 /* Lower-triangular HODLR L with L L^T = Z (H-Cholesky of a symmetric
@@ -317,7 +321,10 @@ int sp_qdwh_params_paper(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, i
  * count = (2b+1) n - b^2 - b.  ab: device pointer. */
 int sp_givens_generate(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double scale, double* cs);
 /* Q1 and Q2 of [scale * A; I] = [Q1; Q2] R in HODLR format on A's tree
- * (Remark "construct_off", Theorems 4 and 6: off-diagonal ranks <= 2b). */
+ * (Remark "construct_off", Theorems 4 and 6: off-diagonal ranks <= 2b).
+ * Q2's blocks are returned recompressed (orthonormal V, U = Q Sigma, at A's
+ * tolerance): the nested-basis factors can differ in scale by many orders of
+ * magnitude for localised eigenvectors, which costs products accuracy. */
 int sp_fastqr_factors(sp_ctx_t ctx, sp_hodlr_t A, double scale, sp_hodlr_t* Q1, sp_hodlr_t* Q2);
 
 #ifdef __cplusplus

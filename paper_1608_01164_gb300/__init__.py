@@ -36,6 +36,7 @@ EXPORTS = [
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
     "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector", "sp_hodlr_level_ranks",
     "sp_trace_product_band", "sp_qdwh_params_paper",
+    "sp_hodlr_transpose",
 ]
 
 
@@ -116,6 +117,7 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_hodlr_destroy": (None, [P]),
         "sp_hodlr_add": (I, [P, D, P, D, P, D, PP]),
         "sp_hodlr_mult": (I, [P, P, P, PP]),
+        "sp_hodlr_transpose": (I, [P, P, PP]),
         "sp_hodlr_cholesky": (I, [P, P, PP]),
         "sp_hodlr_trsm": (I, [P, P, I, P, PP]),
         "sp_inertia": (I, [P, I64, I32, P, I64, I32, P, P]),
@@ -279,6 +281,12 @@ def sp_hodlr_destroy(M):
 def sp_hodlr_add(ctx, alpha, A, beta, B, gamma):
     h = ctypes.c_void_p()
     _check(ctx, _lib.sp_hodlr_add(ctx, float(alpha), A, float(beta), B, float(gamma), ctypes.byref(h)))
+    return h
+
+
+def sp_hodlr_transpose(ctx, M):
+    h = ctypes.c_void_p()
+    _check(ctx, _lib.sp_hodlr_transpose(ctx, M, ctypes.byref(h)))
     return h
 
 

@@ -801,6 +801,11 @@ int sp_hodlr_mult(sp_ctx_t ctx, sp_hodlr_t A, sp_hodlr_t B, sp_hodlr_t* C) {
   });
 }
 
+int sp_hodlr_transpose(sp_ctx_t ctx, sp_hodlr_t M, sp_hodlr_t* T) {
+  if (!ctx || !M || !T) return SP_EINVAL;
+  return guarded(ctx, [&] { *T = hodlr_transpose(ctx, M); });
+}
+
 int sp_hodlr_cholesky(sp_ctx_t ctx, sp_hodlr_t Z, sp_hodlr_t* L) {
   if (!ctx || !Z || !L) return SP_EINVAL;
   return guarded(ctx, [&] {

@@ -439,6 +439,7 @@ struct ClusterSmem {
   double Xpan[kCMaxNB][kCB][kCP];  // row panel X_pj of the current step
   double Linv[kCB][kCP];           // inverse of this CTA's latest diagonal block
   double Lcp[kCB][kCP];            // copy of the current step's L_pp^{-1}
+  double yv[kCB];                  // reciprocals of the diagonal block's pivots
 };
 
 __device__ __forceinline__ int blk_q(int i, int j) { return i * (i + 1) / 2 + j; }
@@ -446,69 +447,68 @@ __device__ __forceinline__ int blk_owner(int i, int j) { return blk_q(i, j) % kC
 __device__ __forceinline__ int blk_slot(int i, int j) { return blk_q(i, j) / kCC; }
 
 // Factor the 16 x 16 diagonal block D (row-major, ld kCP, lower triangle) in
-// place and write its inverse to Linv (zero above the diagonal).  One full
-// warp; lanes 16..31 mirror lanes 0..15 and write nothing.
-__device__ __noinline__ void cluster_diag_block(double* D, double (*Linv)[kCP], int* flags) {
-  const unsigned full = 0xffffffffu;
-  const int i = threadIdx.x & 15;
-  const bool writer = (threadIdx.x & 31) < 16;
-  double row[kCB];
-#pragma unroll
-  for (int k = 0; k < kCB; ++k) row[k] = (k <= i) ? D[i * kCP + k] : 0.0;
-  double yi = 1.0;  // 1 / L_ii of this lane's row
+// place and write its inverse to Linv (zero above the diagonal), with the
+// CTA's first four warps: on this part a binary64 warp instruction occupies
+// its sub-partition's FP64 pipe for many cycles, so one warp per
+// sub-partition (not one warp in all) carries the column chain.  Thread t of
+// 0..127 owns entries (r, c0) and (r, c0 + 8), r = t % 16, c0 = t / 16.
+// Column step j: the pivot's reciprocal square root (computed by every
+// thread from the shared pivot), the column scaled, then the trailing entries
+// updated; two 128-thread barriers per column.  Then the inverse by rows of
+// the forward substitution L X = I (X_kk = 1/L_kk), one barrier per row.
+__device__ __forceinline__ void bar128() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ void cluster_diag_block(double (*D)[kCP], double (*Linv)[kCP], double* yv, int* flags) {
+  const int t = threadIdx.x;
+  const int r = t & 15, c0 = t >> 4, c1 = c0 + 8;
   bool bad = false;
-#pragma unroll
   for (int j = 0; j < kCB; ++j) {
-    double d = __shfl_sync(full, row[j], j);  // pivot: lane j's diagonal entry
+    double d = D[j][j];
     if (!(d > 0.0)) {
       bad = true;
       d = 1.0;
     }
-    const double yj = rsqrt(d);
-    if (i > j) {
-      row[j] *= yj;
-    } else if (i == j) {
-      row[j] = d * yj;
-      yi = yj;
+    const double y = rsqrt(d);
+    bar128();  // every thread has read the pivot before it is overwritten
+    if (c0 == j || c1 == j) {
+      if (r > j) D[r][j] *= y;
+      else if (r == j) {
+        D[j][j] = d * y;
+        yv[j] = y;
+      }
     }
-#pragma unroll
-    for (int k = j + 1; k < kCB; ++k) {
-      const double lkj = __shfl_sync(full, row[j], k);
-      if (i > j && k <= i) row[k] = fma(-row[j], lkj, row[k]);
-    }
+    bar128();
+    if (c0 > j && c0 <= r) D[r][c0] = fma(-D[r][j], D[c0][j], D[r][c0]);
+    if (c1 > j && c1 <= r) D[r][c1] = fma(-D[r][j], D[c1][j], D[r][c1]);
+    bar128();
   }
-  if (bad && threadIdx.x == 0) atomicOr(&flags[FLAG_BREAKDOWN], 1);
-  // inverse by columns of the substitution: x_i[j] = sum_{k<i} L_ik X_kj;
-  // row k of X is final once every k' < k has been added (X_kk = 1/L_kk)
-  double x[kCB];
-#pragma unroll
-  for (int j = 0; j < kCB; ++j) x[j] = 0.0;
-#pragma unroll
+  if (bad && t == 0) atomicOr(&flags[FLAG_BREAKDOWN], 1);
+  // inverse: s_r[c] = sum_{k<r} L_rk X_kc; row k final after k steps
+  double s0 = 0.0, s1 = 0.0;
+  Linv[r][c0] = 0.0;
+  Linv[r][c1] = 0.0;
   for (int k = 0; k < kCB; ++k) {
-    if (i == k) {
-#pragma unroll
-      for (int j = 0; j < k; ++j) x[j] = -yi * x[j];
-      x[k] = yi;
+    if (r == k) {
+      const double yk = yv[k];
+      Linv[k][c0] = (c0 < k) ? -yk * s0 : (c0 == k ? yk : 0.0);
+      Linv[k][c1] = (c1 < k) ? -yk * s1 : (c1 == k ? yk : 0.0);
     }
-#pragma unroll
-    for (int j = 0; j <= k; ++j) {
-      const double xkj = __shfl_sync(full, x[j], k);
-      if (i > k) x[j] = fma(row[k], xkj, x[j]);
-    }
-  }
-  if (writer) {
-#pragma unroll
-    for (int k = 0; k < kCB; ++k) {
-      Linv[i][k] = (k <= i) ? x[k] : 0.0;
-      D[i * kCP + k] = (k <= i) ? row[k] : 0.0;
+    bar128();
+    if (r > k) {
+      const double l = D[r][k];
+      if (c0 <= k) s0 = fma(l, Linv[k][c0], s0);
+      if (c1 <= k) s1 = fma(l, Linv[k][c1], s1);
     }
   }
+  // the strict upper triangle of D is not part of L
+  if (c0 > r) D[r][c0] = 0.0;
+  if (c1 > r) D[r][c1] = 0.0;
 }
 
 // The diagonal step of the block's owner: factor, then X_pp = L_pp^{-1}.
 __device__ void cluster_diag_step(ClusterSmem& S, int p, int* flags) {
   const int sl = blk_slot(p, p);
-  if (threadIdx.x < 32) cluster_diag_block(&S.A[sl][0][0], S.Linv, flags);
+  if (threadIdx.x < 128) cluster_diag_block(S.A[sl], S.Linv, S.yv, flags);
   __syncthreads();
   const int r = threadIdx.x & 15, c = threadIdx.x >> 4;
   S.X[sl][r][c] = S.Linv[r][c];

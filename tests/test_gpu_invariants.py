@@ -170,3 +170,34 @@ def test_mixed_vs_fp64_1e5(ctx, workload):
                 sp.sp_hodlr_destroy(Pm)
     finally:
         sp.sp_hodlr_destroy(P64)
+
+
+@pytest.mark.parametrize("n,leaf", [(98304, 256), (100000, 256)])
+def test_qr_step_commutes_localised(ctx, n, leaf):
+    """The QR-based first step alone (Eq. (qdwh_qr)) gives X1 = f(X0), a
+    function of A: it must commute with A to rounding.  On the localised
+    Anderson matrices at this size the nested-basis factors of Q2 are badly
+    scaled; without rebalancing them the formatted product Q1 Q2^T lost its
+    upper blocks (commutation 4e-5 at n = 98304)."""
+    (_, ab, nu), = sp_inputs.workload(4, n=n)
+    mu, _, _ = sp.sp_locate_shift(ctx, ab, nu)
+    A = sp.sp_hodlr_from_band(ctx, ab, mu, leaf, 1e-12)
+    opts = sp.sp_qdwh_opts_default()
+    opts.delta = 0.999  # the scalar schedule stops after the first (QR-based) step
+    S, info = sp.sp_qdwh_sign(ctx, A, opts)
+    try:
+        assert info.iters == 1 and info.kind[0] == 1
+        V = np.asfortranarray(sp_inputs.normal(77, n * 4).reshape(4, n).T)
+        SV = np.zeros_like(V, order="F")
+        sp.sp_apply(ctx, S, 4, V, n, SV, n)
+        Ash = ab.copy()
+        Ash[:, 0] -= mu
+        AV = np.asfortranarray(band_matvec(Ash, V))
+        SAV = np.zeros_like(V, order="F")
+        sp.sp_apply(ctx, S, 4, AV, n, SAV, n)
+        comm = np.linalg.norm(band_matvec(Ash, SV) - SAV) / (np.max(np.abs(Ash).sum(axis=1)) * np.linalg.norm(V))
+        print(f"n={n} leaf {leaf}: X1 commutation {comm:.1e}")
+        assert comm <= 1e-13, comm
+    finally:
+        sp.sp_hodlr_destroy(A)
+        sp.sp_hodlr_destroy(S)
