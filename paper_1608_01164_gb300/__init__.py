@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libsp.so")
-SOURCES = ["sp_blas.cu", "sp_lowrank.cu", "sp_hodlr.cu", "sp_qrstep.cu", "sp_param.cu", "sp_api.cu"]
+SOURCES = ["sp_blas.cu", "sp_tc.cu", "sp_lowrank.cu", "sp_hodlr.cu", "sp_qrstep.cu", "sp_param.cu", "sp_api.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 
 SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_EBREAKDOWN, SP_ENONFINITE, SP_ERANK, SP_ETIMEOUT, SP_EINTERNAL = range(9)

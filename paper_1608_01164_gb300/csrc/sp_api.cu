@@ -317,6 +317,7 @@ int sp_ctx_create(void* cuda_stream, sp_alloc_fn alloc, sp_free_fn free_fn, void
         configure_blas_kernels();
         configure_lowrank_kernels();
         configure_param_kernels();
+        configure_tc_kernels();
         configured[ctx->device] = true;
       }
     }
@@ -436,7 +437,7 @@ const char* sp_kernel_name(int kernel) {
   static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_core_svd", "k_gather",
                                          "k_leaf_potrf", "k_leaf_inv", "k_givens", "k_replay_leaf",
                                          "k_replay_track", "k_inertia", "misc", "k_gemm[apply]",
-                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm[fp32]", "host_wait"};
+                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm_tc", "host_wait"};
   return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
 }
 

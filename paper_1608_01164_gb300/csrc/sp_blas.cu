@@ -153,9 +153,8 @@ __device__ __forceinline__ int dsize(int s, const int* p) {
   return s;
 }
 
-// MT = double: binary64 throughout.  MT = float: operands rounded to
-// binary32 when staged, binary32 FMA accumulation, result widened to binary64
-// (the mixed-precision steps; storage stays binary64).
+// MT is the arithmetic type of the tile (binary64 here; the mixed-precision
+// scope runs on the tensor cores instead, sp_tc.cu).
 //
 // The grid is laid out in 64 x 64 output tiles; each CTA then computes only
 // the part of its tile inside the actual (device-resident) m x n: a
@@ -823,15 +822,23 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
   // over a few CTAs is compute-bound on a few SMs.  Small problems (fewer
   // 64 x 64 tiles than SMs) are laid out in 16 x 16 tiles instead, and k is
   // split (chunks of at least 32, resp. 64) until the grid covers the GPU.
+  // The mixed-precision scope runs on the tensor cores in 128 x 64 tiles.
+  const bool tc = ctx->gemm_fp32;
   int te = kGT;
+  if (tc) {
+    maxtiles = 0;
+    for (const auto& t : tasks)
+      maxtiles = std::max(maxtiles, ((t.m + gemm_tc_tile_rows() - 1) / gemm_tc_tile_rows()) *
+                                        ((t.n + gemm_tc_tile_cols() - 1) / gemm_tc_tile_cols()));
+  }
   int64_t ctas = (int64_t)maxtiles * (int64_t)tasks.size();
-  if (ksplit <= 0 && ctas < ctx->num_sms) {
+  if (!tc && ksplit <= 0 && ctas < ctx->num_sms) {
     te = 16;
     maxtiles = 0;
     for (const auto& t : tasks) maxtiles = std::max(maxtiles, ((t.m + 15) / 16) * ((t.n + 15) / 16));
     ctas = (int64_t)maxtiles * (int64_t)tasks.size();
   }
-  const int kmin = te == kGT ? 64 : 32;
+  const int kmin = (te == kGT || tc) ? 64 : 32;
   if (ksplit <= 0) {
     if (maxk >= 2 * kmin && ctas < 2 * ctx->num_sms) {
       nz = (int)std::min<int64_t>((4 * ctx->num_sms + ctas - 1) / ctas, maxk / kmin);
@@ -844,19 +851,6 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     kchunk = ((maxk + nz - 1) / nz + kGK - 1) / kGK * kGK;
     nz = (maxk + kchunk - 1) / kchunk;
   }
-  // split k: every chunk writes its partial tile into the task's workspace
-  // slots (nz static m x n slots), a second kernel sums them in order
-  DBuf ws;
-  if (nz > 1) {
-    size_t tot = 0;
-    for (const auto& t : tasks) tot += (size_t)nz * t.m * t.n;
-    ws = DBuf(tot * sizeof(double) + 16, ctx->stream);
-    double* w = ws.as<double>();
-    for (auto& t : tasks) {
-      t.W = w;
-      w += (size_t)nz * t.m * t.n;
-    }
-  }
   int64_t maxe = 1;
   for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
   for (size_t off = 0; off < tasks.size(); off += 65535) {
@@ -868,11 +862,8 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     double* fc = fc_ptr(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
     ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
     const int sp = nz > 1 ? 1 : 0;
-    if (ctx->gemm_fp32) {
-      if (!ta && !tb) k_gemm<false, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else if (ta && !tb) k_gemm<true, false, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else if (!ta && tb) k_gemm<false, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else k_gemm<true, true, float><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+    if (tc) {
+      launch_gemm_tc(ctx, ta, tb, grid, dt, kchunk, sp, fc);
     } else {
       if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
       else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);

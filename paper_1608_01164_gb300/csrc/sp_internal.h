@@ -223,6 +223,15 @@ struct GemmTask {
   double* W;  // split-k partial tiles (set by gemm_batched)
 };
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks, int ksplit = 0);
+// Split-BF16 tensor-core GEMM of the mixed-precision scope (sp_tc.cu): tiles of
+// gemm_tc_tile_rows() x gemm_tc_tile_cols(), gemm_tc_smem() bytes of dynamic
+// shared memory per CTA; split = 1 writes k-chunk partials to the tasks' W.
+size_t gemm_tc_smem();
+int gemm_tc_tile_rows();
+int gemm_tc_tile_cols();
+void launch_gemm_tc(sp_ctx* ctx, bool ta, bool tb, dim3 grid, const GemmTask* tasks, int kchunk, int split,
+                    double* fc);
+void configure_tc_kernels();
 inline GemmTask gt(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int m, int n,
                    int k, double alpha, double beta, const int* pm = nullptr, const int* pn = nullptr,
                    const int* pk = nullptr) {
