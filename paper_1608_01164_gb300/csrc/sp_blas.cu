@@ -851,6 +851,21 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
     kchunk = ((maxk + nz - 1) / nz + kGK - 1) / kGK * kGK;
     nz = (maxk + kchunk - 1) / kchunk;
   }
+  // split k: every chunk writes its partial tile into the task's workspace
+  // slots (nz static m x n slots), a second kernel sums them in order
+  DBuf ws;
+  if (nz > 1) {
+    size_t tot = 0;
+    for (const auto& t : tasks) tot += (size_t)nz * t.m * t.n;
+    ws = DBuf(tot * sizeof(double) + 16, ctx->stream);
+    double* w = ws.as<double>();
+    for (auto& t : tasks) {
+      t.W = w;
+      w += (size_t)nz * t.m * t.n;
+    }
+  }
+  for (const auto& t : tasks)
+    if (nz > 1 && !t.W) fail(SP_EINTERNAL, "split-k GEMM without a workspace");
   int64_t maxe = 1;
   for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
   for (size_t off = 0; off < tasks.size(); off += 65535) {
