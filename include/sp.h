@@ -163,7 +163,7 @@ int64_t sp_launch_count(void);
  * off-diagonal block of the band is stored exactly as a rank-b corner
  * (Lemma 2: a band of width b has off-diagonal rank <= b).
  *   n >= 1; 1 <= b; leaf >= max(2, 2b) (so band corners stay inside sibling
- *   blocks); tol > 0 is the truncation tolerance epsilon of Sec. 3.1.1 and
+ *   blocks), or leaf = 0 for the tuned / rule-based choice (sp_ctx_load_tuning); tol > 0 is the truncation tolerance epsilon of Sec. 3.1.1 and
  *   Sec. 5, an absolute threshold on the singular values of every recompressed
  *   block, kept with the matrix and used by every later formatted operation; rank_cap >= 2b is the per-block
  *   rank capacity (0 selects max(160, 20b)).
@@ -310,6 +310,36 @@ int sp_qdwh_start(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t 
  * SP_EBREAKDOWN if the LU meets an exactly zero pivot (A - mu I singular). */
 int sp_qdwh_params_paper(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu,
                          double* alpha, double* l0, int32_t* iters);
+
+/* ---- autotuning (not in the paper; Sec. 6 fixes n_min by hand) ---- */
+
+typedef struct {
+  int32_t leaf;        /* chosen leaf size (the paper's n_min) */
+  int32_t tsqr_chunk;  /* rows per TSQR chunk of the recompression QR */
+  int32_t small_tiles; /* 1: small GEMMs laid out in 16 x 16 tiles */
+  double ms;           /* time of one projector of the tuning problem with this choice */
+  int32_t trials;      /* projectors timed (0: the answer came from the cache) */
+  int64_t n_tuned;     /* order of the tuning problem (0 when cached) */
+} sp_tune_result;
+
+/* Chooses leaf size, TSQR chunk and GEMM tiling by timing whole projectors
+ * (HODLR ingest, sign by hQDWH in the given precision mode, projector, trace)
+ * of the leading min(n, 16384) block of the band at shift mu: every leaf in
+ * {64, 128, 256, 512} with 2b <= leaf <= half the tuning order, then chunks of
+ * 256 / 512 rows and small tiles on / off at the best leaf.  The result is
+ * appended to cache_path (JSON lines keyed by floor(log2 n), b, precision; may
+ * be NULL) and added to the context's table; a cache hit returns at once with
+ * trials = 0.  ab: host or device.  Synchronising. */
+int sp_autotune(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ldab, double mu, double tol,
+                int32_t precision, const char* cache_path, sp_tune_result* out);
+/* Loads a tuning cache into the context's table (replacing it).  Afterwards
+ * a leaf argument of 0 (sp_hodlr_from_band, sp_batched_projector) takes the
+ * tuned leaf of the nearest size class with the same b, else the rule 64 /
+ * 128 / 256 by n (at least 2b). */
+int sp_ctx_load_tuning(sp_ctx_t ctx, const char* cache_path);
+/* Sets the recompression's TSQR chunk rows (32..8192; default 256) and the
+ * small-problem 16 x 16 GEMM tiling (default on) for the context's calls. */
+int sp_ctx_set_tuning(sp_ctx_t ctx, int32_t tsqr_chunk, int32_t small_tiles);
 
 /* ---- QR-based first iteration (Sec. 4, Algorithms 1/2, Remark "construct_off") ---- */
 

@@ -20,7 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _INCLUDE = os.path.join(os.path.dirname(_HERE), "include")
 LIB_PATH = os.path.join(_HERE, "libsp.so")
-SOURCES = ["sp_blas.cu", "sp_tc.cu", "sp_lowrank.cu", "sp_hodlr.cu", "sp_qrstep.cu", "sp_param.cu", "sp_api.cu"]
+SOURCES = ["sp_blas.cu", "sp_tc.cu", "sp_lowrank.cu", "sp_hodlr.cu", "sp_qrstep.cu", "sp_param.cu", "sp_api.cu",
+           "sp_tune.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC"]
 
 SP_OK, SP_EINVAL, SP_ENOMEM, SP_ECUDA, SP_EBREAKDOWN, SP_ENONFINITE, SP_ERANK, SP_ETIMEOUT, SP_EINTERNAL = range(9)
@@ -36,7 +37,7 @@ EXPORTS = [
     "sp_fastqr_factors", "sp_ctx_set_profiling", "sp_ctx_profile", "sp_ctx_profile_levels", "sp_kernel_name", "sp_kernel_count",
     "sp_launch_count", "sp_inertia_noalloc", "sp_batched_projector", "sp_hodlr_level_ranks",
     "sp_trace_product_band", "sp_qdwh_params_paper",
-    "sp_hodlr_transpose",
+    "sp_hodlr_transpose", "sp_autotune", "sp_ctx_load_tuning", "sp_ctx_set_tuning",
 ]
 
 
@@ -62,6 +63,11 @@ class sp_info(ctypes.Structure):
                 ("ms_combine", ctypes.c_double), ("ms_polish", ctypes.c_double), ("levels", ctypes.c_int),
                 ("max_rank_level", ctypes.c_int * 32), ("mean_rank_level", ctypes.c_double * 32),
                 ("nominal_bytes", ctypes.c_double)]
+
+
+class sp_tune_result(ctypes.Structure):
+    _fields_ = [("leaf", ctypes.c_int32), ("tsqr_chunk", ctypes.c_int32), ("small_tiles", ctypes.c_int32),
+                ("ms", ctypes.c_double), ("trials", ctypes.c_int32), ("n_tuned", ctypes.c_int64)]
 
 
 # stream-ordered allocator callbacks of sp_ctx_create
@@ -118,6 +124,9 @@ def bind(lib: ctypes.CDLL) -> ctypes.CDLL:
         "sp_hodlr_add": (I, [P, D, P, D, P, D, PP]),
         "sp_hodlr_mult": (I, [P, P, P, PP]),
         "sp_hodlr_transpose": (I, [P, P, PP]),
+        "sp_autotune": (I, [P, I64, I32, P, I64, D, D, I32, ctypes.c_char_p, ctypes.POINTER(sp_tune_result)]),
+        "sp_ctx_load_tuning": (I, [P, ctypes.c_char_p]),
+        "sp_ctx_set_tuning": (I, [P, I32, I32]),
         "sp_hodlr_cholesky": (I, [P, P, PP]),
         "sp_hodlr_trsm": (I, [P, P, I, P, PP]),
         "sp_inertia": (I, [P, I64, I32, P, I64, I32, P, P]),
@@ -282,6 +291,23 @@ def sp_hodlr_add(ctx, alpha, A, beta, B, gamma):
     h = ctypes.c_void_p()
     _check(ctx, _lib.sp_hodlr_add(ctx, float(alpha), A, float(beta), B, float(gamma), ctypes.byref(h)))
     return h
+
+
+def sp_autotune(ctx, ab, mu: float, tol: float = 1e-10, precision: int = 0, cache_path: str | None = None):
+    """Tuned (leaf, TSQR chunk, small tiles) for this band's size class; see include/sp.h."""
+    n, bp1 = ab.shape
+    r = sp_tune_result()
+    _check(ctx, _lib.sp_autotune(ctx, n, bp1 - 1, _ptr(ab), bp1, float(mu), float(tol), int(precision),
+                                 cache_path.encode() if cache_path else None, ctypes.byref(r)))
+    return r
+
+
+def sp_ctx_load_tuning(ctx, cache_path: str):
+    _check(ctx, _lib.sp_ctx_load_tuning(ctx, cache_path.encode()))
+
+
+def sp_ctx_set_tuning(ctx, tsqr_chunk: int = 256, small_tiles: bool = True):
+    _check(ctx, _lib.sp_ctx_set_tuning(ctx, int(tsqr_chunk), int(bool(small_tiles))))
 
 
 def sp_hodlr_transpose(ctx, M):

@@ -40,6 +40,7 @@ void hodlr_scale_shift(sp_ctx* ctx, sp_hodlr* M, double alpha, double gamma);
 void inertia_counts_noalloc(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, int nshift,
                             const double* shifts_dev, int64_t* counts_dev);
 int hodlr_max_rank(sp_ctx* ctx, const sp_hodlr* M);
+int tuned_leaf(sp_ctx* ctx, int64_t n, int b);
 void hodlr_level_stats(sp_ctx* ctx, const sp_hodlr* M, int nlevels, int* max_rank, double* mean_rank,
                        double* nominal_bytes);
 void hodlr_check_finite(sp_ctx* ctx, const sp_hodlr* M);
@@ -449,6 +450,7 @@ int sp_hodlr_from_band(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int
                        double tol, int32_t rank_cap, sp_hodlr_t* out) {
   if (!ctx || !out || !ab) return SP_EINVAL;
   if (rank_cap == 0) rank_cap = std::max(160, 20 * b);
+  if (leaf == 0 && n >= 1 && b >= 1) leaf = tuned_leaf(ctx, n, b);
   if (n < 1 || b < 1 || ldab < b + 1 || leaf < 2 || leaf < 2 * b || !(tol > 0.0) || rank_cap < 2 * b) {
     ctx->err = "sp_hodlr_from_band: need n >= 1, b >= 1, ldab >= b+1, leaf >= max(2, 2b), tol > 0, rank_cap >= 2b";
     return SP_EINVAL;
@@ -589,11 +591,6 @@ int sp_qdwh_sign(sp_ctx_t ctx, sp_hodlr_t A, const sp_qdwh_opts* opts_in, sp_hod
   });
 }
 
-static int auto_leaf(int64_t n, int b) {
-  int leaf = n <= 2048 ? 64 : (n <= 8192 ? 128 : 256);
-  return std::max(leaf, std::max(2 * b, 2));
-}
-
 int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const int32_t* b, const double* const* ab,
                          const int64_t* ldab, const double* mu, int32_t leaf, double tol, int32_t rank_cap,
                          const sp_qdwh_opts* opts, int32_t nstreams, sp_hodlr_t* P_out, sp_info* infos) {
@@ -618,6 +615,9 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
     sub.device = ctx->device;
     sub.num_sms = ctx->num_sms;
     sub.alloc = ctx->alloc;
+    sub.tsqr_chunk = ctx->tsqr_chunk;
+    sub.small_tiles = ctx->small_tiles;
+    sub.tuned = ctx->tuned;
     cudaSetDevice(ctx->device);
     cudaStream_t s = nullptr;
     const int src = guarded(&sub, [&] {
@@ -640,7 +640,7 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
       const int i = order[k];
       sp_hodlr_t A = nullptr, S = nullptr, P = nullptr;
       sp_info inf;
-      int rc = sp_hodlr_from_band(&sub, n[i], b[i], ab[i], ldab[i], mu[i], leaf > 0 ? leaf : auto_leaf(n[i], b[i]),
+      int rc = sp_hodlr_from_band(&sub, n[i], b[i], ab[i], ldab[i], mu[i], leaf > 0 ? leaf : tuned_leaf(ctx, n[i], b[i]),
                                   tol, rank_cap, &A);
       if (rc == SP_OK) rc = sp_qdwh_sign(&sub, A, opts, &S, infos ? &inf : nullptr);
       if (rc == SP_OK) rc = sp_projector(&sub, S, &P);

@@ -832,7 +832,7 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
                                         ((t.n + gemm_tc_tile_cols() - 1) / gemm_tc_tile_cols()));
   }
   int64_t ctas = (int64_t)maxtiles * (int64_t)tasks.size();
-  if (!tc && ksplit <= 0 && ctas < ctx->num_sms) {
+  if (!tc && ctx->small_tiles && ksplit <= 0 && ctas < ctx->num_sms) {
     te = 16;
     maxtiles = 0;
     for (const auto& t : tasks) maxtiles = std::max(maxtiles, ((t.m + 15) / 16) * ((t.n + 15) / 16));

@@ -102,7 +102,16 @@ struct sp_ctx {
   // algorithmic flops the kernels count themselves (d_fc[kid])
   bool profiling = false;
   int gemm_kid = sp::KID_GEMM;  // profiler bucket of k_gemm launches (call site)
-  bool gemm_fp32 = false;       // mixed-precision scope: k_gemm computes in binary32
+  bool gemm_fp32 = false;       // mixed-precision scope: GEMMs on the tensor cores
+  // tunables (sp_ctx_set_tuning / sp_autotune): rows per TSQR chunk of the
+  // recompression (at least twice the stacked width), small-problem 16 x 16
+  // GEMM tiles on/off, and the tuned leaf sizes by (log2 n, b, precision)
+  int tsqr_chunk = 256;
+  bool small_tiles = true;
+  struct TunedLeaf {
+    int nbucket, b, precision, leaf, tsqr_chunk, small_tiles;
+  };
+  std::vector<TunedLeaf> tuned;
   double* d_fc = nullptr;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
   int64_t launches[sp::KID_COUNT] = {};

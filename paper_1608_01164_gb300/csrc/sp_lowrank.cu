@@ -640,10 +640,10 @@ struct TreePlan {
 static void plan_side(double* W, int64_t ldw, int rows, const int* pR, int Rmax, double* rdst, int64_t ldr,
                       const double* S, const int* pk, int cap, double* out, int64_t ldo,
                       std::vector<std::vector<QrJob>>& qrl, std::vector<std::vector<ApplyJob>>& apl,
-                      std::vector<DBuf>& keep, cudaStream_t st) {
+                      std::vector<DBuf>& keep, cudaStream_t st, int chunk_rows) {
   // chunks of at least 2 Rmax rows, so that a merge (<= 2 Rmax rows) is never
   // taller than a chunk
-  const int kChunk = std::max(256, (2 * Rmax + 31) / 32 * 32);
+  const int kChunk = std::max(chunk_rows, (2 * Rmax + 31) / 32 * 32);
   struct Node {
     double* J;
     int64_t ldj;
@@ -814,8 +814,8 @@ void recompress(sp_ctx* ctx, const std::vector<LrBlock>& blocks, double tol) {
     cp += (size_t)Rr * b.cap;
     double* SV = cp;
     cp += (size_t)Rr * b.cap;
-    plan_side(g.WU, b.m, b.m, g.R, Rm, RU, Rr, SU, b.rank_out, b.cap, b.Uout, b.ldu_out, qrl, apl, keep, st);
-    plan_side(g.WV, b.q, b.q, g.R, Rm, RV, Rr, SV, b.rank_out, b.cap, b.Vout, b.ldv_out, qrl, apl, keep, st);
+    plan_side(g.WU, b.m, b.m, g.R, Rm, RU, Rr, SU, b.rank_out, b.cap, b.Uout, b.ldu_out, qrl, apl, keep, st, ctx->tsqr_chunk);
+    plan_side(g.WV, b.q, b.q, g.R, Rm, RV, Rr, SV, b.rank_out, b.cap, b.Vout, b.ldv_out, qrl, apl, keep, st, ctx->tsqr_chunk);
     // M = R_U R_V^T (ru x rv, inner dimension R)
     core.push_back(gt(RU, Rr, RV, Rr, M, Rr, Rr, Rr, Rm, 1.0, 0.0, g.ru, g.rv, g.R));
     keep.emplace_back((size_t)Rr * Rr * 3 * sizeof(double) + 16, st);
