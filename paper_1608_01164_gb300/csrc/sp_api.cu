@@ -438,7 +438,8 @@ const char* sp_kernel_name(int kernel) {
   static const char* names[KID_COUNT] = {"k_gemm", "k_qr", "k_apply_q", "k_core_svd", "k_gather",
                                          "k_leaf_potrf", "k_leaf_inv", "k_givens", "k_replay_leaf",
                                          "k_replay_track", "k_inertia", "misc", "k_gemm[apply]",
-                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm_tc", "host_wait"};
+                                         "k_gemm[chol]", "k_gemm[mult]", "k_gemm_tc",
+                                         "k_leaf_chol_inv_cluster", "host_wait"};
   return (kernel >= 0 && kernel < KID_COUNT) ? names[kernel] : "";
 }
 

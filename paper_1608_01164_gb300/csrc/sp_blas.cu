@@ -17,6 +17,7 @@
 #include <stdexcept>
 #include <unordered_map>
 
+#include <vector>
 #include "sp_internal.h"
 
 namespace sp {
@@ -165,12 +166,19 @@ template <bool TA, bool TB, typename MT, int MI, int MJ>
 __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int row0, int col0, int kbeg, int kend,
                                           int split, MT (*As)[kGT + 1], MT (*Bs)[kGT + 1]) {
   constexpr int TM = 16 * MI, TN = 16 * MJ;
+  // independent partial sums per output (up to 16 accumulators a thread):
+  // the k range is otherwise one dependent FMA chain per output, ~160 cycles
+  // a link on this part, which is what a small GEMM on few SMs waits for;
+  // summed in a fixed order at the end
+  constexpr int NP = (16 / (MI * MJ)) < 4 ? 16 / (MI * MJ) : 4;
   const int tid = threadIdx.x, r = tid & 15, c = tid >> 4;
-  MT acc[MI][MJ];
+  MT acc[NP][MI][MJ];
 #pragma unroll
-  for (int i = 0; i < MI; ++i)
+  for (int p = 0; p < NP; ++p)
 #pragma unroll
-    for (int j = 0; j < MJ; ++j) acc[i][j] = (MT)0;
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) acc[p][i][j] = (MT)0;
   for (int kb = kbeg; kb < kend; kb += kGK) {
     for (int e = tid; e < TM * kGK; e += 256) {
       int row, kk;
@@ -199,17 +207,23 @@ __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int r
 #pragma unroll
       for (int i = 0; i < MI; ++i)
 #pragma unroll
-        for (int j = 0; j < MJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < MJ; ++j) acc[kk % NP][i][j] = fma(a[i], b[j], acc[kk % NP][i][j]);
     }
     __syncthreads();
   }
+#pragma unroll
+  for (int p = 1; p < NP; ++p)
+#pragma unroll
+    for (int i = 0; i < MI; ++i)
+#pragma unroll
+      for (int j = 0; j < MJ; ++j) acc[0][i][j] += acc[p][i][j];
 #pragma unroll
   for (int i = 0; i < MI; ++i)
 #pragma unroll
     for (int j = 0; j < MJ; ++j) {
       const int gr = row0 + r + 16 * i, gc = col0 + c + 16 * j;
       if (gr < m && gc < n) {
-        const double v = t.alpha * (double)acc[i][j];
+        const double v = t.alpha * (double)acc[0][i][j];
         if (split) {
           // partial tile of k chunk blockIdx.z (static m x n slot per chunk)
           t.W[(size_t)blockIdx.z * (size_t)t.m * (size_t)t.n + gr + (int64_t)gc * t.m] = v;
@@ -952,9 +966,9 @@ bool leaf_chol_inv(sp_ctx* ctx, const std::vector<LeafTask>& tasks) {
     const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
     std::vector<LeafTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
     DBuf d = upload(part, ctx->stream);
-    ProfScope ps(ctx, KID_POTRF);
+    ProfScope ps(ctx, KID_LEAF_CLUSTER);
     k_leaf_chol_inv_cluster<<<dim3(kCC, (unsigned)cnt), 256, sizeof(ClusterSmem), ctx->stream>>>(
-        d.as<LeafTask>(), ctx->d_flags, fc_ptr(ctx, KID_POTRF), fc_ptr(ctx, KID_LEAF_INV));
+        d.as<LeafTask>(), ctx->d_flags, fc_ptr(ctx, KID_LEAF_CLUSTER), fc_ptr(ctx, KID_LEAF_CLUSTER));
     check_launch("k_leaf_chol_inv_cluster");
   }
   return true;

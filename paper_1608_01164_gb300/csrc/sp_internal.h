@@ -86,7 +86,8 @@ namespace sp {
 // Kernel families timed and flop-counted by the profiler.
 enum KernelId {
   KID_GEMM = 0, KID_QR, KID_APPLYQ, KID_CORE_SVD, KID_GATHER, KID_POTRF, KID_LEAF_INV, KID_GIVENS, KID_REPLAY_LEAF,
-  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_HOST_WAIT, KID_COUNT
+  KID_REPLAY_TRACK, KID_INERTIA, KID_MISC, KID_GEMM_APPLY, KID_GEMM_CHOL, KID_GEMM_MULT, KID_GEMM_F32, KID_LEAF_CLUSTER, KID_HOST_WAIT,
+  KID_COUNT
 };
 }  // namespace sp
 

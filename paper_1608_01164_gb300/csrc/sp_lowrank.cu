@@ -312,16 +312,22 @@ __device__ void block_argmax(const double* v, int c0, int c1, double* red_v, int
     red_i[warp] = bi;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = -1.0;
-    int ib = c1;
-    for (int w = 0; w < nw; ++w)
-      if (red_v[w] > b || (red_v[w] == b && red_i[w] < ib)) {
-        b = red_v[w];
-        ib = red_i[w];
+  if (warp == 0) {  // the per-warp candidates, reduced by one warp
+    double b = lane < nw ? red_v[lane] : -1.0;
+    int ib = lane < nw ? red_i[lane] : c1;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, b, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, ib, o);
+      if (ov > b || (ov == b && oi < ib)) {
+        b = ov;
+        ib = oi;
       }
-    *out_idx = ib;
-    *out_val = b;
+    }
+    if (lane == 0) {
+      *out_idx = ib;
+      *out_val = b;
+    }
   }
   __syncthreads();
 }
@@ -341,19 +347,23 @@ __device__ double make_reflector(double* X, int64_t ld, int j, int rows, double*
   part = warp_sum(part);
   if (lane == 0) red[warp] = part;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double sigma = 0.0;
-    for (int w = 0; w < nw; ++w) sigma += red[w];
+  if (warp == 0) {
+    // the per-warp partials summed by one warp (a fixed order) instead of
+    // one thread's serial sum, then the reflector's scalars (R's diagonal
+    // mu >= 0, as in k_qr)
+    const double sigma = warp_sum(lane < nw ? red[lane] : 0.0);
     const double x0 = X[j + (int64_t)j * ld];
-    if (sigma == 0.0) {
-      s_tau = 0.0;
-      s_v0 = 1.0;
-    } else {
-      const double mu = sqrt(x0 * x0 + sigma);
-      const double v0 = (x0 <= 0.0) ? x0 - mu : -sigma / (x0 + mu);
-      s_tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
-      s_v0 = 1.0 / v0;  // the reciprocal, taken once
-      X[j + (int64_t)j * ld] = mu;
+    if (lane == 0) {
+      if (sigma == 0.0) {
+        s_tau = 0.0;
+        s_v0 = 1.0;
+      } else {
+        const double mu = sqrt(x0 * x0 + sigma);
+        const double v0 = (x0 <= 0.0) ? x0 - mu : -sigma / (x0 + mu);
+        s_tau = 2.0 * v0 * v0 / (sigma + v0 * v0);
+        s_v0 = 1.0 / v0;  // the reciprocal, taken once
+        X[j + (int64_t)j * ld] = mu;
+      }
     }
   }
   __syncthreads();
@@ -441,9 +451,26 @@ __device__ double jacobi_sweeps(T* B, T* J, int ldb, int rp, T eps, int max_swee
         if (valid && gl == 0) fl += 6.0 * rp;
         if (valid && g != (T)0 && g * g > eps * eps * a * b) {
           if (gl == 0) fl += 12.0 * rp;
-          const T zeta = (b - a) / ((T)2 * g);
-          const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          const T cs = (T)1 / sqrt((T)1 + t * t), sn = cs * t;
+          // tan(theta) = t = sign(d) e / (|d| + h), d = b - a, e = 2g,
+          // h = sqrt(d^2 + e^2) (the smaller root of t^2 + 2 (d/e) t - 1);
+          // by the half-angle formulas cos(theta) = (|d| + h) w and
+          // sin(theta) = sign(d) e w with w = 1 / sqrt(2 h (|d| + h)): two
+          // reciprocal square roots on the chain, no division
+          const T d = b - a, e = (T)2 * g;
+          const T hq = fma(d, d, e * e);
+          T cs, sn;
+          if (hq > (T)1e-280 && hq < (T)1e280) {
+            const T h = hq * rsqrt(hq);
+            const T y = fabs(d) + h;
+            const T w = rsqrt((T)2 * h * y);
+            cs = y * w;
+            sn = (d >= (T)0 ? e : -e) * w;
+          } else {  // extreme ranges: the quotient form
+            const T zeta = d / e;
+            const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+            cs = (T)1 / sqrt((T)1 + t * t);
+            sn = cs * t;
+          }
           T* ji = J + (int64_t)i * ldb;
           T* jj2 = J + (int64_t)jj * ldb;
           for (int r = gl; r < rp; r += G) {

@@ -397,8 +397,13 @@ void locate_shift(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t l
 }
 
 // alpha >= ||A - mu I||_2 from brackets of the extreme eigenvalues, l0 from
-// the largest d on a geometric then linear grid with count(mu-d) == count(mu)
-// == count(mu+d) (no eigenvalue within distance d of mu).
+// the largest d on a geometric grid with count(mu-d) == count(mu) ==
+// count(mu+d) (no eigenvalue within distance d of mu).  Every count is an
+// n-long dependent chain (one thread per shift), so all shifts go into one
+// launch: a uniform grid of the Gershgorin interval brackets lambda_1 and
+// lambda_n to 2e-3 of its scale at once, and the grid d_k = a_g 2^(-k/16)
+// (a_g the Gershgorin bound of ||A - mu I||_2) finds the distance to the
+// spectrum within a factor 2^(1/16).
 void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t ldab, double mu, double* alpha,
                 double* l0) {
   double glo, ghi;
@@ -406,44 +411,41 @@ void qdwh_start(sp_ctx* ctx, int64_t n, int b, const double* ab_dev, int64_t lda
   const double pad = 1e-12 * std::max({1.0, std::fabs(glo), std::fabs(ghi)});
   glo -= pad;
   ghi += pad;
-  std::vector<double> x, y;
-  bracket(ctx, n, b, ab_dev, ldab, {1, n}, glo, ghi, 2e-3, x, y);
-  const double lam_min_lo = x[0], lam_max_hi = y[1];
-  const double a = std::max(mu - lam_min_lo, lam_max_hi - mu) * (1.0 + 1e-10);
-  // distance to the spectrum
+  const double scale = std::max({1.0, std::fabs(glo), std::fabs(ghi)});
+  const int P = (int)std::min(4095.0, std::max(255.0, std::ceil((ghi - glo) / (2e-3 * scale))));
+  const double ag = std::max(mu - glo, ghi - mu);
+  constexpr int kSub = 16, kOct = 62;
   std::vector<double> pts;
-  std::vector<double> ds;
   pts.push_back(mu);
-  for (int k = 0; k <= 60; ++k) {
-    const double d = a * std::ldexp(1.0, -k);
+  for (int p = 1; p <= P; ++p) pts.push_back(glo + (ghi - glo) * p / (P + 1));
+  std::vector<double> ds;
+  for (int k = 0; k <= kSub * kOct; ++k) {
+    const double d = ag * std::exp2(-(double)k / kSub);
     ds.push_back(d);
     pts.push_back(mu - d);
     pts.push_back(mu + d);
   }
-  std::vector<int64_t> c = counts_at(ctx, n, b, ab_dev, ldab, pts);
+  const std::vector<int64_t> c = counts_at(ctx, n, b, ab_dev, ldab, pts);
   const int64_t nu = c[0];
+  // lambda_1 >= the largest grid point with count 0; lambda_n < the smallest
+  // grid point with count n (counts are monotone in the shift)
+  double lam_min_lo = glo, lam_max_hi = ghi;
+  for (int p = 1; p <= P; ++p) {
+    if (c[p] == 0) lam_min_lo = pts[p];
+    if (c[p] >= n) {
+      lam_max_hi = pts[p];
+      break;
+    }
+  }
+  const double a = std::max(mu - lam_min_lo, lam_max_hi - mu) * (1.0 + 1e-10);
   double dgood = 0.0;
   for (size_t k = 0; k < ds.size(); ++k) {
-    if (c[1 + 2 * k] == nu && c[2 + 2 * k] == nu) {
+    if (c[1 + P + 2 * k] == nu && c[2 + P + 2 * k] == nu) {
       dgood = ds[k];
       break;
     }
   }
   if (dgood == 0.0) fail(SP_EINVAL, "mu is (numerically) an eigenvalue: no gap found");
-  // refine between dgood and 2 dgood
-  pts.clear();
-  std::vector<double> lin;
-  for (int p = 1; p <= 127; ++p) {
-    const double d = dgood * (1.0 + p / 128.0);
-    lin.push_back(d);
-    pts.push_back(mu - d);
-    pts.push_back(mu + d);
-  }
-  c = counts_at(ctx, n, b, ab_dev, ldab, pts);
-  for (size_t p = 0; p < lin.size(); ++p) {
-    if (c[2 * p] == nu && c[2 * p + 1] == nu) dgood = lin[p];
-    else break;
-  }
   *alpha = a;
   *l0 = std::min(dgood / a, 1.0);
 }

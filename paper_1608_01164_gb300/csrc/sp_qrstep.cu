@@ -339,6 +339,46 @@ __global__ void k_replay_track(const TrackJob* __restrict__ jobs, int njobs, con
   }
 }
 
+// The same tracking for b = 1 with the state in registers.  Per step i the
+// rotations are alpha (columns n, n+i), beta (i, n), gamma (i, i+1).  For a
+// coefficient row the bottom column n+i starts at zero and is not read again,
+// column i+1 starts at zero at its first rotation (gamma of step i), and the
+// basis at the start is {column hi, column n}: so the live state is column
+// i's value and column n's value, and a step is
+//   cn <- c_a cn;  (t, cn) <- (c_b t + s_b cn, -s_b t + c_b cn);
+//   V(i) = c_g t;  t <- -s_g t  (the value of column i+1).
+// Two threads per job (the two basis vectors).
+__global__ void k_replay_track_b1(const TrackJob* __restrict__ jobs, int njobs, const double* __restrict__ cs,
+                                  const int64_t* __restrict__ off, int64_t n) {
+  const int gid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = gid >> 1, t = gid & 1;
+  if (w >= njobs) return;
+  const TrackJob jb = jobs[w];
+  double ti = (t == 0) ? 1.0 : 0.0, cn = (t == 1) ? 1.0 : 0.0;
+  for (int64_t i = jb.hi; i < jb.hi2; ++i) {
+    int64_t idx = off[i];
+    if (i >= 1) {
+      cn = __ldg(cs + 2 * idx) * cn;
+      ++idx;
+    }
+    const double cb = __ldg(cs + 2 * idx), sb = __ldg(cs + 2 * idx + 1);
+    ++idx;
+    const double x = ti;
+    ti = fma(cb, x, sb * cn);
+    cn = fma(-sb, x, cb * cn);
+    double tn = 0.0;
+    if (i + 1 < n) {
+      const double cg = __ldg(cs + 2 * idx), sg = __ldg(cs + 2 * idx + 1);
+      tn = -sg * ti;
+      ti = cg * ti;
+    }
+    jb.V[(i - jb.hi) + (int64_t)t * n] = ti;
+    ti = tn;
+  }
+  jb.E[t] = (jb.hi2 < n) ? ti : 0.0;  // u = 0: column hi2
+  jb.E[t + 2] = cn;                   // u = 1: column n
+}
+
 // right child c: U = b x b corner (first b rows), V = identity tail of the left
 // sibling (rows I_{c-1}), rank b; left child handled by basis GEMMs.
 __global__ void k_corner_blocks(const double* __restrict__ corner, int cs_ld, int64_t n, int b, int cap, double* U,
@@ -434,9 +474,14 @@ void fastqr_factors(sp_ctx* ctx, const sp_hodlr* A, double scale, sp_hodlr** Q1o
       const int nj = (int)tj.size();
       const int per_block = 4;  // 4 jobs x 64 threads
       ProfScope ps(ctx, KID_REPLAY_TRACK);
-      k_replay_track<<<(nj + per_block - 1) / per_block, 64 * per_block, 0, st>>>(d.as<TrackJob>(), nj,
-                                                                                  csb.as<double>(),
-                                                                                  offb.as<int64_t>(), n, b);
+      if (b == 1) {
+        k_replay_track_b1<<<(2 * nj + 127) / 128, 128, 0, st>>>(d.as<TrackJob>(), nj, csb.as<double>(),
+                                                                 offb.as<int64_t>(), n);
+      } else {
+        k_replay_track<<<(nj + per_block - 1) / per_block, 64 * per_block, 0, st>>>(d.as<TrackJob>(), nj,
+                                                                                    csb.as<double>(),
+                                                                                    offb.as<int64_t>(), n, b);
+      }
       check_launch("k_replay_track");
       // bases bottom-up: U_parent(I_c) = U_c E_c (left child), U_parent(I_{c+1}) = U_{c+1}
       for (int l = L; l >= 2; --l) {
