@@ -53,6 +53,11 @@ def parse(argv=None):
     p.add_argument("--n", type=int, default=100000)
     p.add_argument("--leaf", type=int, default=256)
     p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--tsqr-chunk", type=int, default=0,
+                   help="rows of a TSQR chunk in the recompression (0: the library default, 256)")
+    p.add_argument("--autotune", action="store_true",
+                   help="before timing, tune the TSQR chunk and GEMM tiling on the workload's leading block "
+                        "(sp_autotune) and use them; the leaf stays the workload's")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--cpu-sample-n", type=int, default=1536)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -330,6 +335,15 @@ def run_ours(args):
     mu, _, _ = sp.sp_locate_shift(ctx, ab, nu)
     ab_dev = torch.from_numpy(np.ascontiguousarray(ab)).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    tuning = None
+    if args.autotune:
+        r = sp.sp_autotune(ctx, np.ascontiguousarray(ab), mu, args.tol, 0 if args.precision == "fp64" else 1)
+        sp.sp_ctx_set_tuning(ctx, r.tsqr_chunk, bool(r.small_tiles))
+        tuning = {"tsqr_chunk": r.tsqr_chunk, "small_tiles": int(r.small_tiles), "tuned_leaf": r.leaf,
+                  "trials": r.trials, "n_tuned": r.n_tuned}
+    elif args.tsqr_chunk > 0:
+        sp.sp_ctx_set_tuning(ctx, args.tsqr_chunk, True)
+        tuning = {"tsqr_chunk": args.tsqr_chunk, "small_tiles": 1}
 
     opts = sp.sp_qdwh_opts_default()
     if args.precision != "fp64":
@@ -472,7 +486,8 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "s/projector", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f64+f32",
-            "data": "synthetic", "config": config_dict(args, name, ab, nu), "roofline": roofline, "cpu_baseline": cpu,
+            "data": "synthetic", "config": dict(config_dict(args, name, ab, nu), **({"tuning": tuning} if tuning else {})),
+            "roofline": roofline, "cpu_baseline": cpu,
             "e2e": {"value": e2e_s / world if e2e_s else None, "unit": "s/projector", "steps": len(e2e),
                     "h2d_bytes_per_step": int(ab_host.nbytes), "d2h_bytes_per_step": 8},
             "gpu_launches": int(launches), "clocks": clocks,

@@ -281,7 +281,7 @@ __global__ void k_nonfinite(const double* __restrict__ p, size_t count, int* fla
 __global__ void k_splitk_reduce(const GemmTask* __restrict__ tasks, int kchunk) {
   const GemmTask t = tasks[blockIdx.y];
   const int m = dsize(t.m, t.pm), n = dsize(t.n, t.pn), k = dsize(t.k, t.pk);
-  const int nz = k > 0 ? (k + kchunk - 1) / kchunk : 1;
+  const int nz = t.nsplit > 0 ? t.nsplit : (k > 0 ? (k + kchunk - 1) / kchunk : 1);
   const size_t slot = (size_t)t.m * (size_t)t.n;
   const int64_t total = (int64_t)m * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -818,26 +818,115 @@ __global__ void __launch_bounds__(256) k_leaf_inv_smem(const LeafTask* __restric
 }
 }  // namespace
 
+namespace {
+// One GEMM launch (and its split-k reduction) over `tasks`, grid
+// (tiles, tasks, nz), in parts of at most 65535 tasks.
+void gemm_launch(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks, int maxtiles, int te, int nz,
+                 int kchunk, bool split, bool tc) {
+  int64_t maxe = 1;
+  for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
+  for (size_t off = 0; off < tasks.size(); off += 65535) {
+    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
+    std::vector<GemmTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
+    DBuf d = upload(part, ctx->stream);
+    dim3 grid(maxtiles, (unsigned)cnt, nz);
+    const GemmTask* dt = d.as<GemmTask>();
+    double* fc = fc_ptr(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
+    ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
+    const int sp = split ? 1 : 0;
+    if (tc) {
+      launch_gemm_tc(ctx, ta, tb, grid, dt, kchunk, sp, fc);
+    } else {
+      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
+    }
+    check_launch("k_gemm");
+  }
+}
+
+void splitk_reduce(sp_ctx* ctx, const std::vector<GemmTask>& tasks, int kchunk) {
+  int64_t maxe = 1;
+  for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
+  for (size_t off = 0; off < tasks.size(); off += 65535) {
+    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
+    std::vector<GemmTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
+    DBuf d = upload(part, ctx->stream);
+    const int gx = (int)std::min<int64_t>((maxe + 255) / 256, 1024);
+    k_splitk_reduce<<<dim3(gx, (unsigned)cnt), 256, 0, ctx->stream>>>(d.as<GemmTask>(), kchunk);
+    check_launch("k_splitk_reduce");
+  }
+}
+
+// Tasks with a static k above this are cut into k ranges of at most this
+// many rows (binary64 path): a coupling V^T X over a block of n/2 rows would
+// otherwise walk its whole k range in one CTA -- a chain of n/32 dependent
+// 16-deep k stages -- while the grid, sized from the rank capacities, looks
+// large enough to skip the split-k below.
+constexpr int kLongK = 1024;
+}  // namespace
+
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, int ksplit) {
   if (tasks_in.empty()) return;
   std::vector<GemmTask> tasks;
   tasks.reserve(tasks_in.size());
-  int maxtiles = 0, maxk = 0;
+  int maxk = 0;
   for (const auto& t : tasks_in) {
     if (t.m <= 0 || t.n <= 0) continue;
     tasks.push_back(t);
-    maxtiles = std::max(maxtiles, ((t.m + kGT - 1) / kGT) * ((t.n + kGT - 1) / kGT));
     maxk = std::max(maxk, t.k);
     ctx->flops += 2.0 * t.m * (double)t.n * (double)t.k;
   }
   if (tasks.empty()) return;
+  const bool tc = ctx->gemm_fp32;
+  // long static k ranges: sub-tasks of at most kLongK rows, each writing its
+  // own workspace slot; every task of the launch goes through the workspace
+  // (one slot when not cut) and a second kernel sums a task's slots in order
+  bool longk = false;
+  if (!tc && ksplit <= 0)
+    for (const auto& t : tasks) longk |= (!t.pk && t.k > kLongK);
+  if (longk) {
+    auto nsub = [](const GemmTask& t) { return (!t.pk && t.k > kLongK) ? (t.k + kLongK - 1) / kLongK : 1; };
+    size_t tot = 0;
+    for (const auto& t : tasks) tot += (size_t)nsub(t) * t.m * t.n;
+    DBuf ws(tot * sizeof(double) + 16, ctx->stream);
+    double* w = ws.as<double>();
+    std::vector<GemmTask> sub, red;
+    int maxtiles = 0, kch = 1;
+    for (const auto& t : tasks) {
+      const int ns = nsub(t);
+      GemmTask r = t;
+      r.W = w;
+      r.nsplit = ns;
+      red.push_back(r);
+      for (int z = 0; z < ns; ++z) {
+        GemmTask s = t;
+        if (ns > 1) {
+          const int kb = z * kLongK;
+          s.k = std::min(kLongK, t.k - kb);
+          s.A = ta ? t.A + kb : t.A + (int64_t)kb * t.lda;
+          s.B = tb ? t.B + (int64_t)kb * t.ldb : t.B + kb;
+        }
+        s.W = w + (size_t)z * t.m * t.n;
+        sub.push_back(s);
+        kch = std::max(kch, s.k);
+        maxtiles = std::max(maxtiles, ((t.m + kGT - 1) / kGT) * ((t.n + kGT - 1) / kGT));
+      }
+      w += (size_t)ns * t.m * t.n;
+    }
+    gemm_launch(ctx, ta, tb, sub, maxtiles, kGT, 1, kch, true, false);
+    splitk_reduce(ctx, red, kch);
+    return;
+  }
+  int maxtiles = 0;
+  for (const auto& t : tasks) maxtiles = std::max(maxtiles, ((t.m + kGT - 1) / kGT) * ((t.n + kGT - 1) / kGT));
   int nz = 1, kchunk = std::max(maxk, 1);
   // binary64 runs at about 8 GFLOP/s per SM on this part, so a GEMM spread
   // over a few CTAs is compute-bound on a few SMs.  Small problems (fewer
   // 64 x 64 tiles than SMs) are laid out in 16 x 16 tiles instead, and k is
   // split (chunks of at least 32, resp. 64) until the grid covers the GPU.
   // The mixed-precision scope runs on the tensor cores in 128 x 64 tiles.
-  const bool tc = ctx->gemm_fp32;
   int te = kGT;
   if (tc) {
     maxtiles = 0;
@@ -880,32 +969,8 @@ void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& ta
   }
   for (const auto& t : tasks)
     if (nz > 1 && !t.W) fail(SP_EINTERNAL, "split-k GEMM without a workspace");
-  int64_t maxe = 1;
-  for (const auto& t : tasks) maxe = std::max<int64_t>(maxe, (int64_t)t.m * t.n);
-  for (size_t off = 0; off < tasks.size(); off += 65535) {
-    const size_t cnt = std::min<size_t>(65535, tasks.size() - off);
-    std::vector<GemmTask> part(tasks.begin() + off, tasks.begin() + off + cnt);
-    DBuf d = upload(part, ctx->stream);
-    dim3 grid(maxtiles, (unsigned)cnt, nz);
-    const GemmTask* dt = d.as<GemmTask>();
-    double* fc = fc_ptr(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
-    ProfScope ps(ctx, ctx->gemm_fp32 ? KID_GEMM_F32 : ctx->gemm_kid);
-    const int sp = nz > 1 ? 1 : 0;
-    if (tc) {
-      launch_gemm_tc(ctx, ta, tb, grid, dt, kchunk, sp, fc);
-    } else {
-      if (!ta && !tb) k_gemm<false, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else if (ta && !tb) k_gemm<true, false, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else if (!ta && tb) k_gemm<false, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-      else k_gemm<true, true, double><<<grid, 256, 0, ctx->stream>>>(dt, kchunk, sp, te, fc);
-    }
-    check_launch("k_gemm");
-    if (nz > 1) {
-      const int gx = (int)std::min<int64_t>((maxe + 255) / 256, 1024);
-      k_splitk_reduce<<<dim3(gx, (unsigned)cnt), 256, 0, ctx->stream>>>(dt, kchunk);
-      check_launch("k_splitk_reduce");
-    }
-  }
+  gemm_launch(ctx, ta, tb, tasks, maxtiles, te, nz, kchunk, nz > 1, tc);
+  if (nz > 1) splitk_reduce(ctx, tasks, kchunk);
 }
 
 void axpby_batched(sp_ctx* ctx, const std::vector<AxpbyTask>& tasks) {

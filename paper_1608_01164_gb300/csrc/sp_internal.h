@@ -231,6 +231,7 @@ struct GemmTask {
   const int* pk;
   double alpha, beta;
   double* W;  // split-k partial tiles (set by gemm_batched)
+  int nsplit = 0;  // reduction: number of W slots of this task (0: from k and the launch's k chunk)
 };
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks, int ksplit = 0);
 // Split-BF16 tensor-core GEMM of the mixed-precision scope (sp_tc.cu): tiles of
