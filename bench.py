@@ -578,6 +578,8 @@ def run_batched(args):
     prof = sp.sp_ctx_profile(ctx)
     sp.sp_ctx_set_profiling(ctx, False)
     table = kernel_table(prof, 0)
+    if not table:
+        raise RuntimeError("the profiled batch reported no kernel launches")
     kname, kt = next(iter(table.items()))
     achieved = kt.get("tflops", 0.0)
     roofline = {"bound": "alu", "kernel": kname, "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",

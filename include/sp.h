@@ -337,7 +337,7 @@ int sp_autotune(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ld
  * tuned leaf of the nearest size class with the same b, else the rule 64 /
  * 128 / 256 by n (at least 2b). */
 int sp_ctx_load_tuning(sp_ctx_t ctx, const char* cache_path);
-/* Sets the recompression's TSQR chunk rows (32..8192; default 256) and the
+/* Sets the recompression's TSQR chunk rows (32..8192; default 512) and the
  * small-problem 16 x 16 GEMM tiling (default on) for the context's calls. */
 int sp_ctx_set_tuning(sp_ctx_t ctx, int32_t tsqr_chunk, int32_t small_tiles);
 

@@ -306,7 +306,7 @@ def sp_ctx_load_tuning(ctx, cache_path: str):
     _check(ctx, _lib.sp_ctx_load_tuning(ctx, cache_path.encode()))
 
 
-def sp_ctx_set_tuning(ctx, tsqr_chunk: int = 256, small_tiles: bool = True):
+def sp_ctx_set_tuning(ctx, tsqr_chunk: int = 512, small_tiles: bool = True):
     _check(ctx, _lib.sp_ctx_set_tuning(ctx, int(tsqr_chunk), int(bool(small_tiles))))
 
 

@@ -380,6 +380,7 @@ int sp_ctx_set_profiling(sp_ctx_t ctx, int on) {
       ctx->ev[k].clear();
       ctx->launches[k] = 0;
       ctx->ms[k] = 0.0;
+      ctx->fc_host[k] = 0.0;
     }
     for (auto& ne : ctx->chol_ev)
       for (int k = 0; k < ne.nev; ++k) cudaEventDestroy(ne.e[k]);
@@ -410,7 +411,7 @@ int sp_ctx_profile(sp_ctx_t ctx, int kernel, int64_t* launches, double* ms, doub
     }
     if (launches) *launches = ctx->launches[kernel];
     if (ms) *ms = ctx->ms[kernel];
-    if (flops) *flops = h[kernel];
+    if (flops) *flops = h[kernel] + ctx->fc_host[kernel];
   });
 }
 
@@ -619,6 +620,7 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
     sub.tsqr_chunk = ctx->tsqr_chunk;
     sub.small_tiles = ctx->small_tiles;
     sub.tuned = ctx->tuned;
+    sub.profiling = ctx->profiling;
     cudaSetDevice(ctx->device);
     cudaStream_t s = nullptr;
     const int src = guarded(&sub, [&] {
@@ -626,6 +628,10 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
       sub.stream = s;
       sub.d_flags = static_cast<int*>(dmalloc(sizeof(int) * NFLAGS, s));
       check_cuda(cudaMemsetAsync(sub.d_flags, 0, sizeof(int) * NFLAGS, s), "worker flags");
+      if (sub.profiling) {
+        sub.d_fc = static_cast<double*>(dmalloc(sizeof(double) * KID_COUNT, s));
+        check_cuda(cudaMemsetAsync(sub.d_fc, 0, sizeof(double) * KID_COUNT, s), "worker profiler counters");
+      }
     });
     if (src != SP_OK) {
       int expect = SP_OK;
@@ -666,11 +672,38 @@ int sp_batched_projector(sp_ctx_t ctx, int32_t nbatch, const int64_t* n, const i
       outs[i]->stream = ctx->stream;
       outs[i]->tree->stream = ctx->stream;
     }
+    if (sub.profiling) {
+      // fold the worker's launch times, launch counts and flop counters into
+      // the caller's context (its kernels ran concurrently with the other
+      // workers', so the times add up to more than the wall time)
+      double hfc[KID_COUNT] = {};
+      if (sub.d_fc) cudaMemcpy(hfc, sub.d_fc, sizeof(hfc), cudaMemcpyDeviceToHost);
+      for (int k = 0; k < KID_COUNT; ++k) {
+        for (auto& e : sub.ev[k]) {
+          float t = 0.f;
+          if (cudaEventElapsedTime(&t, e.first, e.second) == cudaSuccess) sub.ms[k] += t;
+          cudaEventDestroy(e.first);
+          cudaEventDestroy(e.second);
+        }
+        sub.ev[k].clear();
+      }
+      for (auto& ne : sub.chol_ev)
+        for (int k = 0; k < ne.nev; ++k) cudaEventDestroy(ne.e[k]);
+      sub.chol_ev.clear();
+      std::lock_guard<std::mutex> lk(mu_err);
+      for (int k = 0; k < KID_COUNT; ++k) {
+        ctx->ms[k] += sub.ms[k];
+        ctx->launches[k] += sub.launches[k];
+        ctx->fc_host[k] += hfc[k];
+      }
+    }
     {
       AllocScope scope(&sub.alloc);
       dfree(sub.d_flags, s);
+      dfree(sub.d_fc, s);
     }
     sub.d_flags = nullptr;
+    sub.d_fc = nullptr;
     cudaStreamSynchronize(s);
     cudaStreamDestroy(s);
   };

@@ -864,7 +864,7 @@ void splitk_reduce(sp_ctx* ctx, const std::vector<GemmTask>& tasks, int kchunk) 
 // otherwise walk its whole k range in one CTA -- a chain of n/32 dependent
 // 16-deep k stages -- while the grid, sized from the rank capacities, looks
 // large enough to skip the split-k below.
-constexpr int kLongK = 1024;
+constexpr int kLongK = 512;
 }  // namespace
 
 void gemm_batched(sp_ctx* ctx, bool ta, bool tb, const std::vector<GemmTask>& tasks_in, int ksplit) {

@@ -107,13 +107,14 @@ struct sp_ctx {
   // tunables (sp_ctx_set_tuning / sp_autotune): rows per TSQR chunk of the
   // recompression (at least twice the stacked width), small-problem 16 x 16
   // GEMM tiles on/off, and the tuned leaf sizes by (log2 n, b, precision)
-  int tsqr_chunk = 256;
+  int tsqr_chunk = 512;
   bool small_tiles = true;
   struct TunedLeaf {
     int nbucket, b, precision, leaf, tsqr_chunk, small_tiles;
   };
   std::vector<TunedLeaf> tuned;
   double* d_fc = nullptr;
+  double fc_host[sp::KID_COUNT] = {};  // flops folded in from batched workers' contexts
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[sp::KID_COUNT];
   int64_t launches[sp::KID_COUNT] = {};
   double ms[sp::KID_COUNT] = {};

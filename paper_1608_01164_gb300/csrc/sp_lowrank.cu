@@ -8,7 +8,7 @@
 //   1. gather the stacked factors  W_U = [U_1 .. U_S]  (m x R) and
 //      W_V = [s_1 V_1 .. s_S V_S]  (q x R);
 //   2. Householder QR of W_U and W_V; tall factors use a binary TSQR tree of
-//      256-row chunks (every chunk and merge is one CTA), so a block of 50 000
+//      512-row chunks (tunable; every chunk and merge is one CTA), so a block of 50 000
 //      rows spreads over many SMs.  A merge stacks its children's R factors
 //      compactly: its row count and the children's row offsets follow from the
 //      actual width R on the device, so no stage works on padding;

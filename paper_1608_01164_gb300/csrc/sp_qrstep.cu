@@ -347,16 +347,20 @@ __global__ void k_replay_track(const TrackJob* __restrict__ jobs, int njobs, con
 // i's value and column n's value, and a step is
 //   cn <- c_a cn;  (t, cn) <- (c_b t + s_b cn, -s_b t + c_b cn);
 //   V(i) = c_g t;  t <- -s_g t  (the value of column i+1).
+// Step i's first rotation has index 0 (i = 0) or 3i - 1 (steps 0 and n-1 have
+// two rotations, the others three), so the rotation loads do not wait on an
+// offset load and the unrolled loop issues them ahead of the state's chain.
 // Two threads per job (the two basis vectors).
 __global__ void k_replay_track_b1(const TrackJob* __restrict__ jobs, int njobs, const double* __restrict__ cs,
-                                  const int64_t* __restrict__ off, int64_t n) {
+                                  int64_t n) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   const int w = gid >> 1, t = gid & 1;
   if (w >= njobs) return;
   const TrackJob jb = jobs[w];
   double ti = (t == 0) ? 1.0 : 0.0, cn = (t == 1) ? 1.0 : 0.0;
+#pragma unroll 4
   for (int64_t i = jb.hi; i < jb.hi2; ++i) {
-    int64_t idx = off[i];
+    int64_t idx = (i == 0) ? 0 : 3 * i - 1;
     if (i >= 1) {
       cn = __ldg(cs + 2 * idx) * cn;
       ++idx;
@@ -475,8 +479,7 @@ void fastqr_factors(sp_ctx* ctx, const sp_hodlr* A, double scale, sp_hodlr** Q1o
       const int per_block = 4;  // 4 jobs x 64 threads
       ProfScope ps(ctx, KID_REPLAY_TRACK);
       if (b == 1) {
-        k_replay_track_b1<<<(2 * nj + 127) / 128, 128, 0, st>>>(d.as<TrackJob>(), nj, csb.as<double>(),
-                                                                 offb.as<int64_t>(), n);
+        k_replay_track_b1<<<(2 * nj + 127) / 128, 128, 0, st>>>(d.as<TrackJob>(), nj, csb.as<double>(), n);
       } else {
         k_replay_track<<<(nj + per_block - 1) / per_block, 64 * per_block, 0, st>>>(d.as<TrackJob>(), nj,
                                                                                     csb.as<double>(),

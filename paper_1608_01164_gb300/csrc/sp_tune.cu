@@ -7,7 +7,7 @@
 // GPU: the projector of a tuning problem (the leading min(n, 16384) block of
 // the caller's band, same shift) is timed for every candidate leaf size in
 // {64, 128, 256, 512} (at least 2b, at most half the tuning order), then, at
-// the best leaf, for TSQR chunks of 256 and 512 rows and with the 16 x 16
+// the best leaf, for TSQR chunks of 256, 512 and 1024 rows and with the 16 x 16
 // small-problem GEMM tiles on and off (coordinate descent).  Results are kept
 // in a cache file of JSON lines keyed by (floor(log2 n), b, precision), read
 // back by sp_ctx_load_tuning; a leaf argument of 0 then takes the tuned leaf.
@@ -145,14 +145,14 @@ int sp_autotune(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ld
     return rc;
   };
   double ms = 0.0;
-  int rc = run(std::max(64, 2 * b), 256, true, &ms);  // warm-up (first-touch allocations)
+  int rc = run(std::max(64, 2 * b), 512, true, &ms);  // warm-up (first-touch allocations)
   std::vector<int> leaves;
   for (int leaf : {64, 128, 256, 512})
     if (leaf >= 2 * b && leaf <= std::max<int64_t>(nt / 2, 2 * b)) leaves.push_back(leaf);
   int best_leaf = leaves.empty() ? 2 * b : leaves[0];
   double best = 1e300;
   for (int leaf : leaves) {
-    const int r = run(leaf, 256, true, &ms);
+    const int r = run(leaf, 512, true, &ms);
     if (r != SP_OK) {
       rc = r;
       continue;
@@ -163,13 +163,14 @@ int sp_autotune(sp_ctx_t ctx, int64_t n, int32_t b, const double* ab, int64_t ld
       best_leaf = leaf;
     }
   }
-  int best_chunk = 256;
+  int best_chunk = 512;
   bool best_tiles = true;
   if (best < 1e300) {
-    if (run(best_leaf, 512, true, &ms) == SP_OK && ms < best) {
-      best = ms;
-      best_chunk = 512;
-    }
+    for (int chunk : {256, 1024})
+      if (run(best_leaf, chunk, true, &ms) == SP_OK && ms < best) {
+        best = ms;
+        best_chunk = chunk;
+      }
     if (run(best_leaf, best_chunk, false, &ms) == SP_OK && ms < best) {
       best = ms;
       best_tiles = false;

@@ -106,3 +106,23 @@ def test_batched_concurrent_kernel_limits(ctx):
     finally:
         for P in Ps:
             sp.sp_hodlr_destroy(P)
+
+
+def test_batched_profile_reaches_the_callers_context(ctx):
+    """The worker contexts' launch times, counts and flop counters are folded
+    into the caller's context, so a profiled batch reports its kernels."""
+    inst = batch_instances(3, 911)
+    shifts = [oracle.locate_mu(ab, nu) for ab, nu in inst]
+    sp.sp_ctx_set_profiling(ctx, True)
+    try:
+        Ps, _ = sp.sp_batched_projector(ctx, [np.ascontiguousarray(ab) for ab, _ in inst], [s.mu for s in shifts],
+                                        leaf=64, tol=1e-10, nstreams=2)
+        for P in Ps:
+            sp.sp_hodlr_destroy(P)
+        prof = sp.sp_ctx_profile(ctx)
+    finally:
+        sp.sp_ctx_set_profiling(ctx, False)
+    la, ms, fl = prof["k_qr"]
+    assert la > 0 and ms > 0.0 and fl > 0.0
+    gemm = [v for k, v in prof.items() if k.startswith("k_gemm")]
+    assert sum(v[0] for v in gemm) > 0 and sum(v[2] for v in gemm) > 0.0
