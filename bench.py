@@ -50,7 +50,8 @@ def parse(argv=None):
     p.add_argument("--polish", type=int, default=1)
     p.add_argument("--batch", type=int, default=256)
     p.add_argument("--nstreams", type=int, default=16)
-    p.add_argument("--n", type=int, default=100000)
+    p.add_argument("--n", type=int, default=None,
+                   help="order of the band (default: 32768 for band16, 100000 otherwise)")
     p.add_argument("--leaf", type=int, default=256)
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--tsqr-chunk", type=int, default=0,
@@ -64,7 +65,10 @@ def parse(argv=None):
     p.add_argument("--mixed-steps", type=int, default=2,
                    help="timed steps of the mixed-precision (Newton-Schulz tail) form measured beside the binary64 "
                         "run, with ||P_mixed - P_fp64||_2 by power iteration (0: skip)")
-    return p.parse_args(argv)
+    args = p.parse_args(argv)
+    if args.n is None:
+        args.n = 32768 if args.workload == "band16" else 100000
+    return args
 
 
 def workload_band(args, rank):
