@@ -167,7 +167,7 @@ __device__ __forceinline__ void gemm_tile(const GemmTask& t, int m, int n, int r
                                           int split, MT (*As)[kGT + 1], MT (*Bs)[kGT + 1]) {
   constexpr int TM = 16 * MI, TN = 16 * MJ;
   // independent partial sums per output (up to 16 accumulators a thread):
-  // the k range is otherwise one dependent FMA chain per output, ~160 cycles
+  // the k range is otherwise one dependent FMA chain per output, 64 cycles
   // a link on this part, which is what a small GEMM on few SMs waits for;
   // summed in a fixed order at the end
   constexpr int NP = (16 / (MI * MJ)) < 4 ? 16 / (MI * MJ) : 4;
